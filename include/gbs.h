@@ -1,0 +1,137 @@
+/*
+ * gbs.h -- C ABI of libgbs: stage-1 tables of a Gaussian boson sampling emulator
+ * (arXiv:2511.14923, Sec. "Pre-computing the cumulants" and App. "Correlators of
+ * GBS with binary outcomes") on NVIDIA GB300 (sm_103a).
+ *
+ * Given the 2M x 2M covariance V of a zero-mean Gaussian state (hbar = 2, xxpp:
+ * mode k owns rows/cols k and k+M), the library fills tables over every mode
+ * subset S with 1 <= |S| <= kmax <= 5:
+ *
+ *   vacuum probability  P0(S)  = det[(V_S + I)/2]^{-1/2}
+ *                        (Eq. vacuum_gaussian_prob with zero mean and hbar = 2;
+ *                         V_S keeps rows/cols k and k+M for k in S)
+ *   click moment        mu(S)  = p(every mode of S clicks)
+ *                              = sum_{T subset S} (-1)^{|T|} P0(T)
+ *                        (Eq. joint_moments_def / Eq. joint_moments_threshold)
+ *   click cumulant      kt(S)  = sum over set partitions pi of S of
+ *                                (-1)^{|pi|-1} (|pi|-1)! prod_{b in pi} mu(b)
+ *                        (Eq. joint_cumulants_def)
+ *
+ * TABLE LAYOUT. A table has gbs_table_size(M, kmax) = sum_{d=1..kmax} C(M,d)
+ * entries (FP64). Entries are grouped by order d (d = 1 first); the order-d group
+ * starts at gbs_order_offset(M, d) and holds the d-subsets in colex order: the
+ * sorted set c_1 < c_2 < ... < c_d (0-based modes) sits at rank
+ * sum_{i=1..d} C(c_i, i). The empty set is not stored.
+ *
+ * MEMORY. Every pointer passed to a compute entry point (V, outputs, gradients,
+ * workspace) is a CUDA device pointer owned by the caller; it must stay valid
+ * until the work queued on cuda_stream completes. The library never allocates
+ * device memory, never frees caller memory and never throws across the ABI.
+ * Each compute call needs a caller-provided workspace of at least
+ * gbs_workspace_bytes(M, kmax, precision) bytes, 256-byte aligned; one workspace
+ * must not be used by two calls that may run at the same time.
+ *
+ * ERRORS. Argument errors are detected on the host before anything is queued
+ * and return a nonzero gbs_status (gbs_last_error() gives a message). Device
+ * errors (a non-positive-definite reduced covariance) are recorded in a status
+ * word inside the workspace; the affected entries are NaN. gbs_stream_status()
+ * synchronises the stream and returns that status.
+ *
+ * STREAMS. cuda_stream is a cudaStream_t (NULL = legacy default stream). Calls
+ * are asynchronous with respect to the host; calls on one stream run in order.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBS_OK = 0,
+    GBS_ERR_INVALID_ARG = 1,  /* bad M, kmax, precision, null or misaligned pointer */
+    GBS_ERR_NOT_POSDEF = 2,   /* some (V_T + I)/2 is not positive definite (device) */
+    GBS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    GBS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up (batched launch) */
+    GBS_ERR_WORKSPACE = 5     /* workspace smaller than gbs_workspace_bytes() */
+} gbs_status;
+
+typedef enum {
+    /* every determinant step in FP64 */
+    GBS_FP64 = 0,
+    /* determinant steps as FP32 Cholesky steps refined once to FP64 accuracy
+       (log det += tr(L^{-1} E L^{-T}), residual E formed exactly from FP32
+       products); inclusion-exclusion and partition sums stay in FP64 */
+    GBS_FP32_REFINED = 1
+} gbs_precision;
+
+#define GBS_MAX_ORDER 5
+#define GBS_MAX_MODES 1024
+
+/* ---------------------------------------------------------------- host helpers */
+
+/* Number of table entries: sum_{d=1..kmax} C(M, d); 0 if the arguments are invalid
+   (M < 1, M > GBS_MAX_MODES, kmax < 1, kmax > min(M, GBS_MAX_ORDER)). */
+uint64_t gbs_table_size(int M, int kmax);
+
+/* First entry of the order-d group: sum_{e<d} C(M, e), e >= 1. 0 for invalid d. */
+uint64_t gbs_order_offset(int M, int d);
+
+/* Colex rank of a sorted mode set modes[0] < ... < modes[d-1]: sum C(modes[i], i+1).
+   Returns UINT64_MAX if modes is NULL, d is out of [1, GBS_MAX_ORDER] or the
+   modes are not strictly increasing and non-negative. */
+uint64_t gbs_rank(const int *modes, int d);
+
+/* Inverse of gbs_rank: writes the d sorted modes of rank r to modes_out.
+   Returns GBS_OK or GBS_ERR_INVALID_ARG. */
+int gbs_unrank(uint64_t r, int d, int *modes_out);
+
+/* Workspace bytes needed by any compute call with these (M, kmax, precision) on
+   the current CUDA device; 0 if the arguments are invalid. */
+size_t gbs_workspace_bytes(int M, int kmax, int precision);
+
+/* Message for the most recent failing call on this host thread ("" if none). */
+const char *gbs_last_error(void);
+
+/* Synchronises cuda_stream, then returns the device status recorded in the
+   workspace by the calls queued on it (GBS_OK, GBS_ERR_NOT_POSDEF, ...), or
+   GBS_ERR_CUDA if the synchronisation itself failed. The status is cleared by
+   the next compute call that uses the workspace. */
+int gbs_stream_status(const void *workspace, void *cuda_stream);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Per-order kernel timing. While enabled (on != 0), every forward call records
+   CUDA events on its stream before and after the kernels of each order.
+   gbs_timing_read() waits for the events of the most recent call and writes
+   durations in milliseconds: ms_out[0] = packing (V -> 2x2 blocks), ms_out[d] =
+   the kernels of order d (d = 1..GBS_MAX_ORDER; 0 for orders above kmax).
+   Events are created on first use; timing state is process-wide and not meant
+   for concurrent calls from several host threads. Returns GBS_OK or GBS_ERR_CUDA. */
+int gbs_timing(int on);
+int gbs_timing_read(float *ms_out);
+
+/* ---------------------------------------------------------------- forward tables */
+
+/* P0 table: p0_out[gbs_table_size(M,kmax)] <- P0(S) for every 1 <= |S| <= kmax
+   (Eq. vacuum_gaussian_prob, hbar = 2, zero mean). V: 2M x 2M row-major FP64,
+   symmetric, xxpp. */
+int gbs_vacuum_probs(const double *V, int M, int kmax, double *p0_out, int precision,
+                     void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Click-moment table: mu_out[...] <- mu(S) (Eq. joint_moments_def with the
+   threshold-detector moments of Eq. joint_moments_threshold). */
+int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int precision,
+                      void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Click-cumulant table: kappa_out[...] <- kt(S) (Eq. joint_cumulants_def). */
+int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
+                  void *workspace, size_t ws_bytes, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBS_H */

@@ -176,8 +176,10 @@ static double partition_weight(int nblocks) {
    joint_cumulants_def; the same map takes correlators to spin cumulants,
    Eq. cumulant_corr_main). */
 double orc_cumulant_from_moments(const double *mom, int d) {
-    static const int cap = 4140; /* B_8 */
-    int *parts = (int *)malloc(sizeof(int) * cap * ORC_MAXD);
+    static const int bell[ORC_MAXD + 1] = {1, 1, 2, 5, 15, 52, 203, 877, 4140};
+    if (d <= 0 || d > ORC_MAXD) return NAN;
+    const int cap = bell[d];
+    int *parts = (int *)malloc(sizeof(int) * cap * d);
     int np = orc_set_partitions(d, parts, cap);
     double acc = 0.0;
     for (int p = 0; p < np; ++p) {

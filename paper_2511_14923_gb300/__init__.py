@@ -1,0 +1,173 @@
+"""GB300-native stage-1 tables of the Gaussian boson sampling emulator of
+arXiv:2511.14923: vacuum probabilities, click moments and click cumulants of a
+zero-mean Gaussian state over every mode subset of size <= kmax <= 5.
+
+This module is a thin ctypes binding over ``libgbs.so`` (C ABI in
+``include/gbs.h``): it checks tensor arguments, allocates outputs and the
+workspace through PyTorch (device memory and streams only) and calls the
+library. Every step of the computation runs in the library's CUDA kernels; if
+the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from math import comb
+
+import torch
+
+__all__ = [
+    "GbsError", "lib", "build", "table_size", "order_offset", "rank", "unrank", "workspace_bytes",
+    "Workspace", "vacuum_probs", "click_moments", "cumulants", "PRECISIONS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libgbs.so")
+_lib = None
+
+PRECISIONS = {"fp64": 0, "fp32r": 1}
+STATUS = {0: "GBS_OK", 1: "GBS_ERR_INVALID_ARG", 2: "GBS_ERR_NOT_POSDEF", 3: "GBS_ERR_CUDA",
+          4: "GBS_ERR_TIMEOUT", 5: "GBS_ERR_WORKSPACE"}
+
+
+class GbsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgbs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2511_14923_gb300.build() "
+                          "(nvcc, sm_103a); there is no fallback implementation")
+    L = ctypes.CDLL(_LIB_PATH)
+    u64, i32, vp, sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+    L.gbs_table_size.argtypes = [i32, i32]; L.gbs_table_size.restype = u64
+    L.gbs_order_offset.argtypes = [i32, i32]; L.gbs_order_offset.restype = u64
+    L.gbs_rank.argtypes = [ctypes.POINTER(i32), i32]; L.gbs_rank.restype = u64
+    L.gbs_unrank.argtypes = [u64, i32, ctypes.POINTER(i32)]; L.gbs_unrank.restype = i32
+    L.gbs_workspace_bytes.argtypes = [i32, i32, i32]; L.gbs_workspace_bytes.restype = sz
+    L.gbs_last_error.argtypes = []; L.gbs_last_error.restype = ctypes.c_char_p
+    L.gbs_stream_status.argtypes = [vp, vp]; L.gbs_stream_status.restype = i32
+    L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
+    L.gbs_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float)]; L.gbs_timing_read.restype = i32
+    for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants"):
+        f = getattr(L, name)
+        f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
+        f.restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise GbsError(rc, lib().gbs_last_error().decode())
+
+
+def table_size(M: int, kmax: int) -> int:
+    return int(lib().gbs_table_size(M, kmax))
+
+
+def order_offset(M: int, d: int) -> int:
+    return int(lib().gbs_order_offset(M, d))
+
+
+def rank(modes) -> int:
+    arr = (ctypes.c_int * len(modes))(*[int(m) for m in modes])
+    return int(lib().gbs_rank(arr, len(modes)))
+
+
+def unrank(r: int, d: int) -> list[int]:
+    arr = (ctypes.c_int * d)()
+    _check(lib().gbs_unrank(r, d, arr))
+    return list(arr)
+
+
+def workspace_bytes(M: int, kmax: int, precision: str = "fp64") -> int:
+    return int(lib().gbs_workspace_bytes(M, kmax, PRECISIONS[precision]))
+
+
+class Workspace:
+    """Device workspace sized for (M, kmax, precision); reusable across calls on one stream."""
+
+    def __init__(self, M: int, kmax: int, precision: str = "fp64", device=None):
+        n = workspace_bytes(M, kmax, precision)
+        if n == 0:
+            raise GbsError(1, f"invalid (M={M}, kmax={kmax}, precision={precision})")
+        self.buf = torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+        self.nbytes = n
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def status(self, stream=None) -> int:
+        st = stream or torch.cuda.current_stream(self.buf.device)
+        return int(lib().gbs_stream_status(ctypes.c_void_p(self.ptr), ctypes.c_void_p(st.cuda_stream)))
+
+
+def _prep(V: torch.Tensor):
+    if not isinstance(V, torch.Tensor) or V.dtype != torch.float64 or not V.is_cuda:
+        raise TypeError("V must be a CUDA float64 tensor")
+    if V.dim() != 2 or V.shape[0] != V.shape[1] or V.shape[0] % 2:
+        raise ValueError("V must be 2M x 2M")
+    return V.contiguous(), V.shape[0] // 2
+
+
+def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, workspace, check: bool):
+    V, M = _prep(V)
+    n = table_size(M, kmax)
+    if n == 0:
+        raise GbsError(1, f"invalid (M={M}, kmax={kmax})")
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=V.device)
+    elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
+    ws = workspace or Workspace(M, kmax, precision, device=V.device)
+    st = torch.cuda.current_stream(V.device)
+    f = getattr(lib(), fname)
+    _check(f(ctypes.c_void_p(V.data_ptr()), M, kmax, ctypes.c_void_p(out.data_ptr()), PRECISIONS[precision],
+             ctypes.c_void_p(ws.ptr), ws.nbytes, ctypes.c_void_p(st.cuda_stream)))
+    if check:
+        _check(ws.status(st))
+    return out
+
+
+def vacuum_probs(V, kmax, precision="fp64", out=None, workspace=None, check=True):
+    """P0(S) = det[(V_S + I)/2]^{-1/2} for every 1 <= |S| <= kmax (table layout of gbs.h)."""
+    return _forward("gbs_vacuum_probs", V, kmax, precision, out, workspace, check)
+
+
+def click_moments(V, kmax, precision="fp64", out=None, workspace=None, check=True):
+    """mu(S) = probability that every mode of S clicks, for every 1 <= |S| <= kmax."""
+    return _forward("gbs_click_moments", V, kmax, precision, out, workspace, check)
+
+
+def cumulants(V, kmax, precision="fp64", out=None, workspace=None, check=True):
+    """Joint click cumulants kt(S) for every 1 <= |S| <= kmax."""
+    return _forward("gbs_cumulants", V, kmax, precision, out, workspace, check)
+
+
+def timing(on: bool) -> None:
+    """Enable or disable per-order CUDA-event timing inside the library."""
+    _check(lib().gbs_timing(1 if on else 0))
+
+
+def timing_read() -> list[float]:
+    """[pack, order 1, .., order 5] kernel milliseconds of the most recent timed call."""
+    arr = (ctypes.c_float * 6)()
+    _check(lib().gbs_timing_read(arr))
+    return list(arr)
+
+
+def n_subsets(M: int, kmax: int) -> int:
+    return sum(comb(M, d) for d in range(1, kmax + 1))

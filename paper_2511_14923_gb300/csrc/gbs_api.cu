@@ -1,0 +1,217 @@
+// Host side of the libgbs C ABI (include/gbs.h): argument validation, workspace
+// layout and kernel launches. No function here allocates device memory.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "gbs.h"
+#include "gbs_common.cuh"
+#include "gbs_fwd.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+// Profiling events (gbs_timing): ev[0..1] around packing, ev[d+1] after order d.
+bool g_timing = false;
+bool g_timing_used = false;
+cudaEvent_t g_ev[GBS_MAX_ORDER + 2];
+bool g_ev_ready = false;
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int ok() {
+    g_err[0] = '\0';
+    return GBS_OK;
+}
+
+bool valid_mk(int M, int kmax) {
+    return M >= 1 && M <= GBS_MAX_MODES && kmax >= 1 && kmax <= GBS_MAX_ORDER && kmax <= M;
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+// True if p is memory the current device can dereference (device or managed).
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_common(const double *V, int M, int kmax, const void *out, int precision, void *ws, size_t ws_bytes,
+                 gbs::WsLayout &L, int &sms) {
+    if (!valid_mk(M, kmax))
+        return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d and 1 <= kmax <= min(M, %d); got M=%d kmax=%d",
+                    GBS_MAX_MODES, GBS_MAX_ORDER, M, kmax);
+    if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
+        return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
+    if (!V || !out || !ws) return fail(GBS_ERR_INVALID_ARG, "V, output and workspace must be non-NULL");
+    if (((uintptr_t)V & 7) || ((uintptr_t)out & 7))
+        return fail(GBS_ERR_INVALID_ARG, "V and the output must be 8-byte aligned");
+    if ((uintptr_t)ws & 255) return fail(GBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (!is_device_ptr(V) || !is_device_ptr(out) || !is_device_ptr(ws))
+        return fail(GBS_ERR_INVALID_ARG, "V, output and workspace must be CUDA device (or managed) memory");
+    sms = device_sms();
+    if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
+    L = gbs::ws_layout(M, kmax, sms);
+    if (ws_bytes < L.total)
+        return fail(GBS_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.total);
+    return GBS_OK;
+}
+
+int run_forward(int mode, const double *V, int M, int kmax, double *out, int precision, void *ws, size_t ws_bytes,
+                void *stream) {
+    gbs::WsLayout L;
+    int sms = 0;
+    int rc = check_common(V, M, kmax, out, precision, ws, ws_bytes, L, sms);
+    if (rc != GBS_OK) return rc;
+    if (precision == GBS_FP32_REFINED)
+        return fail(GBS_ERR_INVALID_ARG, "GBS_FP32_REFINED is not available in this build");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *w = static_cast<char *>(ws);
+    cudaError_t e = cudaMemsetAsync(w + L.status_off, 0, 256, st);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    gbs::FwdArgs a{};
+    a.V = V;
+    a.M = M;
+    a.kmax = kmax;
+    a.mode = mode;
+    a.precision = precision;
+    a.A = reinterpret_cast<double *>(w + L.A_off);
+    a.p0 = (mode == gbs::MODE_P0) ? out : reinterpret_cast<double *>(w + L.p0_off);
+    a.out = out;
+    a.status = reinterpret_cast<unsigned *>(w + L.status_off);
+    a.counters = a.status + 8;
+    a.scratch = reinterpret_cast<double *>(w + L.scratch_off);
+    a.slot_doubles = L.slot_doubles;
+    a.slots = L.slots;
+    a.sms = sms;
+    a.ev = nullptr;
+    if (g_timing) {
+        if (!g_ev_ready) {
+            for (auto &ev : g_ev)
+                if ((e = cudaEventCreate(&ev)) != cudaSuccess)
+                    return fail(GBS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+            g_ev_ready = true;
+        }
+        a.ev = g_ev;
+        g_timing_used = true;
+    }
+    e = gbs::launch_forward(a, st);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t gbs_table_size(int M, int kmax) {
+    if (!valid_mk(M, kmax)) return 0;
+    return gbs::order_offset(M, kmax + 1);
+}
+
+uint64_t gbs_order_offset(int M, int d) {
+    if (M < 1 || M > GBS_MAX_MODES || d < 1 || d > GBS_MAX_ORDER || d > M) return 0;
+    return gbs::order_offset(M, d);
+}
+
+uint64_t gbs_rank(const int *modes, int d) {
+    if (!modes || d < 1 || d > GBS_MAX_ORDER) return UINT64_MAX;
+    uint64_t r = 0;
+    for (int i = 0; i < d; ++i) {
+        if (modes[i] < 0 || modes[i] >= GBS_MAX_MODES || (i > 0 && modes[i] <= modes[i - 1])) return UINT64_MAX;
+        r += gbs::binom(modes[i], i + 1);
+    }
+    return r;
+}
+
+int gbs_unrank(uint64_t r, int d, int *modes_out) {
+    if (!modes_out || d < 1 || d > GBS_MAX_ORDER) return fail(GBS_ERR_INVALID_ARG, "bad d or NULL output");
+    if (r >= gbs::binom(GBS_MAX_MODES, d)) return fail(GBS_ERR_INVALID_ARG, "rank out of range");
+    for (int k = d; k >= 1; --k) {
+        // largest c with C(c, k) <= r, by bisection over [k-1, GBS_MAX_MODES)
+        int lo = k - 1, hi = GBS_MAX_MODES;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) / 2;
+            if (gbs::binom(mid, k) <= r) lo = mid;
+            else hi = mid;
+        }
+        modes_out[k - 1] = lo;
+        r -= gbs::binom(lo, k);
+    }
+    return ok();
+}
+
+size_t gbs_workspace_bytes(int M, int kmax, int precision) {
+    if (!valid_mk(M, kmax) || (precision != GBS_FP64 && precision != GBS_FP32_REFINED)) return 0;
+    const int sms = device_sms();
+    return gbs::ws_layout(M, kmax, sms > 0 ? sms : 1).total;
+}
+
+const char *gbs_last_error(void) { return g_err; }
+
+int gbs_timing(int on) {
+    g_timing = on != 0;
+    return ok();
+}
+
+int gbs_timing_read(float *ms_out) {
+    if (!ms_out) return fail(GBS_ERR_INVALID_ARG, "NULL output");
+    if (!g_ev_ready || !g_timing_used) return fail(GBS_ERR_INVALID_ARG, "no timed call has been made");
+    cudaError_t e = cudaEventSynchronize(g_ev[GBS_MAX_ORDER + 1]);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+    for (int i = 0; i <= GBS_MAX_ORDER; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, g_ev[i], g_ev[i + 1]);
+        if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
+        ms_out[i] = ms;
+    }
+    return ok();
+}
+
+int gbs_stream_status(const void *workspace, void *cuda_stream) {
+    if (!workspace) return fail(GBS_ERR_INVALID_ARG, "NULL workspace");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    unsigned s = 0;
+    e = cudaMemcpy(&s, workspace, sizeof s, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "reading the status word: %s", cudaGetErrorString(e));
+    if (s & gbs::ST_TIMEOUT) return fail(GBS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (s & gbs::ST_NOT_POSDEF)
+        return fail(GBS_ERR_NOT_POSDEF, "a reduced covariance (V_T + I)/2 is not positive definite");
+    if (s & gbs::ST_BAD_INDEX) return fail(GBS_ERR_INVALID_ARG, "a device index check failed");
+    return ok();
+}
+
+int gbs_vacuum_probs(const double *V, int M, int kmax, double *p0_out, int precision, void *workspace,
+                     size_t ws_bytes, void *cuda_stream) {
+    return run_forward(gbs::MODE_P0, V, M, kmax, p0_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int precision, void *workspace,
+                      size_t ws_bytes, void *cuda_stream) {
+    return run_forward(gbs::MODE_MU, V, M, kmax, mu_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
+                  size_t ws_bytes, void *cuda_stream) {
+    return run_forward(gbs::MODE_KAPPA, V, M, kmax, kappa_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+}  // extern "C"

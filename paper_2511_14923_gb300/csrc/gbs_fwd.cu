@@ -1,0 +1,558 @@
+// Forward kernels of libgbs: vacuum probabilities P0(S), click moments mu(S) and
+// click cumulants kt(S) over all subsets of order 1..kmax (arXiv:2511.14923,
+// Eq. vacuum_gaussian_prob, Eq. joint_moments_def, Eq. joint_cumulants_def).
+//
+// Order d is computed after orders < d, whose tables it reads.
+//
+//   Determinant (every order). For S = {j} + S' with j = min S, the Schur
+//   complement step det A_S = det A_{S'} * det(Sch_j) gives
+//   P0(S) = P0(S') * det(Sch_j)^{-1/2}, with P0(S') read from the order-(d-1)
+//   table. Sch_j is the 2x2 block of j after Gaussian elimination of the modes
+//   of S' from A = (V+I)/2.
+//
+//   Click moment. Splitting the subsets T of S by whether they contain j:
+//     mu(S) = mu(S') - sum_{T' subset S'} (-1)^{|T'|} P0({j} + T').
+//
+//   Click cumulant. With y_k = 1 - x_k the no-click indicators, the joint
+//   moments of y are the P0 values and, by translation invariance and
+//   homogeneity of cumulants (the argument of Eq. cumulant_exponential),
+//   kt(S) = (-1)^{|S|} ky(S) for |S| >= 2, where ky is the cumulant of y. The
+//   block-containing-j recursion of Eq. correlators_expanded_2, applied to y,
+//   ky(S) = P0(S) - sum_{R proper subset of S'} ky(R + {j}) P0(S' - R),
+//   then gives, with ky({j}) = P0({j}) and ky(Q) = (-1)^{|Q|} kt(Q) otherwise,
+//     kt(S) = (-1)^{|S|} [ P0(S) - P0({j}) P0(S')
+//                          + sum_{empty != R proper subset S'} (-1)^{|R|} kt(R + {j}) P0(S' - R) ].
+//   This is the partition sum of Eq. joint_cumulants_def organised by the block
+//   that holds j: 2^{d-1} - 1 products per entry instead of one per partition.
+//
+// Kernels
+//   pack_kernel     A = (V+I)/2 as M x M packed 2x2 blocks (xxpp rows k, k+M).
+//   order1/2/3      one thread per subset; the elimination is redone per thread.
+//   tree_kernel<D>  D = 4, 5: persistent CTAs walk the colex prefix tree. A CTA
+//                   owns U = {c_4, .., c_D} and stores the Schur complement of
+//                   A after eliminating U (modes below c_4) in its scratch slot.
+//                   For each child P = {c_3} + U it eliminates c_3 once per
+//                   mode x < c_3 (z(x), d(x), the c_2 pivots) into shared
+//                   memory; each leaf (c_2, j) then costs one 2x2 cross update,
+//                   one 2x2 triangular solve and one 2x2 Schur step.
+#include <cstdio>
+
+#include "gbs.h"
+#include "gbs_common.cuh"
+#include "gbs_fwd.cuh"
+
+namespace gbs {
+
+constexpr int FLAT_THREADS = 256;
+constexpr int TREE_THREADS = 512;
+constexpr int XCAP = 1152;  // per-batch x-entries in shared memory (>= GBS_MAX_MODES)
+constexpr int CCAP = 64;    // per-batch children
+
+// ---------------------------------------------------------------- shared combine step
+
+// Per-child constants of the gathers. P = {c_3, .., c_D} ascending, NP = D-2
+// elements, subsets of P by bitmask over P's positions.
+//   baseJ[Q]: table index of {x} + Q is baseJ[Q] + x   (x < min P)
+//   baseT[Q]: table index of {j, c2} + Q is baseT[Q] + t, t = C(c2,2) + j
+//   idxQ[Q] : table index of Q (Q nonempty)
+template <int NP>
+__device__ __forceinline__ void child_bases(const int *P, int M, uint64_t *baseJ, uint64_t *baseT, uint64_t *idxQ) {
+    uint64_t off[GBS_MAX_ORDER + 2];
+    off[0] = 0;
+    off[1] = 0;
+    for (int m = 2; m <= NP + 2; ++m) off[m] = off[m - 1] + binom(M, m - 1);
+#pragma unroll
+    for (int q = 0; q < (1 << NP); ++q) {
+        int m = __popc(q);
+        uint64_t sJ = off[m + 1], sT = off[m + 2], sQ = off[m];
+        int i = 0;
+#pragma unroll
+        for (int e = 0; e < NP; ++e)
+            if (q >> e & 1) {
+                ++i;
+                sJ += binom(P[e], i + 1);
+                sT += binom(P[e], i + 2);
+                sQ += binom(P[e], i);
+            }
+        baseJ[q] = sJ;
+        baseT[q] = sT;
+        idxQ[q] = sQ;
+    }
+}
+
+// Mode-specific value of the leaf S = {j, c2} + P (|P| = NP) given P0(S).
+// p0R[R] = P0(R) for nonempty R subset of P.
+template <int NP, int MODE>
+__device__ __forceinline__ double combine(double P0S, int j, int c2, uint32_t t, const uint64_t *baseJ,
+                                          const uint64_t *baseT, const double *p0R, const double *__restrict__ p0tab,
+                                          const double *__restrict__ outtab) {
+    constexpr int PALL = (1 << NP) - 1;
+    if (MODE == MODE_P0) return P0S;
+    if (MODE == MODE_MU) {
+        double acc = outtab[baseJ[PALL] + c2];  // mu(S')
+#pragma unroll
+        for (int q = 0; q <= PALL; ++q) {
+            const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
+            acc = fma(-sg, p0tab[baseJ[q] + j], acc);
+            const double t2 = (q == PALL) ? P0S : p0tab[baseT[q] + t];
+            acc = fma(sg, t2, acc);
+        }
+        return acc;
+    }
+    // MODE_KAPPA
+    double acc = fma(-p0tab[j], p0tab[baseJ[PALL] + c2], P0S);
+#pragma unroll
+    for (int q = 1; q <= PALL; ++q) {
+        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
+        acc = fma(sg * outtab[baseJ[q] + j], p0tab[baseJ[PALL ^ q] + c2], acc);
+    }
+#pragma unroll
+    for (int q = 0; q < PALL; ++q) {
+        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
+        acc = fma(-sg * outtab[baseT[q] + t], p0R[PALL ^ q], acc);
+    }
+    return ((NP + 2) & 1) ? -acc : acc;
+}
+
+// ---------------------------------------------------------------- small kernels
+
+__global__ void pack_kernel(const double *__restrict__ V, int M, double *__restrict__ A) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * M) return;
+    const int x = idx / M, y = idx - x * M;
+    const size_t n2 = 2 * (size_t)M;
+    double a00 = V[x * n2 + y], a01 = V[x * n2 + y + M];
+    double a10 = V[(x + M) * n2 + y], a11 = V[(x + M) * n2 + y + M];
+    if (x == y) {
+        a00 += 1.0;
+        a11 += 1.0;
+    }
+    store_blk(A + 4 * (size_t)idx, Blk{0.5 * a00, 0.5 * a01, 0.5 * a10, 0.5 * a11});
+}
+
+template <int MODE>
+__global__ void order1_kernel(FwdArgs a, bool write_p0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.M) return;
+    const Sym s = blk_sym(ablk(a.A, a.M, j, j));
+    const double det = det_sym(s);
+    double P0 = rsqrt(det);
+    if (!(det > 0.0) || !(s.s00 > 0.0)) {
+        flag_status(a.status, ST_NOT_POSDEF);
+        P0 = __longlong_as_double(0x7ff8000000000000ULL);
+    }
+    if (write_p0) a.p0[j] = P0;
+    if (MODE != MODE_P0) a.out[j] = 1.0 - P0;  // mu({j}) = kt({j}) = 1 - P0({j})
+}
+
+template <int MODE>
+__global__ void order2_kernel(FwdArgs a, bool write_p0) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int M = a.M;
+    if (t >= binom2(M)) return;
+    int c2, j;
+    pair_decode(t, c2, j);
+    bool ok;
+    double detp;
+    const LInv m2 = chol2_inv(blk_sym(ablk(a.A, M, c2, c2)), ok, detp);
+    const Blk w = lmul(m2, ablk(a.A, M, c2, j));
+    const Sym sch = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), w);
+    const double det2 = det_sym(sch);
+    double P0 = a.p0[c2] * rsqrt(det2);
+    if (!(det2 > 0.0) || !ok) {
+        flag_status(a.status, ST_NOT_POSDEF);
+        P0 = __longlong_as_double(0x7ff8000000000000ULL);
+    }
+    const uint64_t idx = (uint64_t)M + t;
+    if (write_p0) a.p0[idx] = P0;
+    if (MODE == MODE_MU) a.out[idx] = a.out[c2] - a.p0[j] + P0;
+    if (MODE == MODE_KAPPA) a.out[idx] = fma(-a.p0[j], a.p0[c2], P0);
+}
+
+template <int MODE>
+__global__ void order3_kernel(FwdArgs a, bool write_p0) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int M = a.M;
+    if (r >= binom(M, 3)) return;
+    int s[3];
+    colex_unrank(r, 3, s);
+    const int j = s[0], c2 = s[1], c3 = s[2];
+    const uint32_t t = (uint32_t)binom2(c2) + j;
+    bool ok3, ok2;
+    double dd;
+    const LInv m3 = chol2_inv(blk_sym(ablk(a.A, M, c3, c3)), ok3, dd);
+    const Blk z2 = lmul(m3, ablk(a.A, M, c3, c2));
+    const Blk zj = lmul(m3, ablk(a.A, M, c3, j));
+    const LInv m2 = chol2_inv(sym_sub_gram(blk_sym(ablk(a.A, M, c2, c2)), z2), ok2, dd);
+    const Sym dj = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), zj);
+    const Blk X = blk_sub_cross(ablk(a.A, M, c2, j), z2, zj);
+    const Sym sch = sym_sub_gram(dj, lmul(m2, X));
+    const double det2 = det_sym(sch);
+    uint64_t baseJ[2], baseT[2], idxQ[2];
+    const int P[1] = {c3};
+    child_bases<1>(P, M, baseJ, baseT, idxQ);
+    double P0 = a.p0[baseJ[1] + c2] * rsqrt(det2);
+    if (!(det2 > 0.0) || !ok3 || !ok2) {
+        flag_status(a.status, ST_NOT_POSDEF);
+        P0 = __longlong_as_double(0x7ff8000000000000ULL);
+    }
+    const double p0R[2] = {0.0, a.p0[idxQ[1]]};
+    const double v = combine<1, MODE>(P0, j, c2, t, baseJ, baseT, p0R, a.p0, a.out);
+    const uint64_t idx = baseT[1] + t;
+    if (write_p0) a.p0[idx] = P0;
+    if (MODE != MODE_P0) a.out[idx] = v;
+}
+
+// ---------------------------------------------------------------- tree kernel
+
+template <int D>
+struct TreeShared {
+    static constexpr int NP = D - 2;       // |P|
+    static constexpr int NQ = 1 << NP;     // subsets of P
+    // item decode
+    uint32_t c4pref[GBS_MAX_MODES + 2];
+    uint32_t item;
+    // uniform pivots of the item's U
+    double upiv[8];
+    // children of the current batch
+    int c3[CCAP];
+    int xoff[CCAP + 1];
+    uint32_t lpref[CCAP + 1];
+    uint64_t baseJ[CCAP][NQ];
+    uint64_t baseT[CCAP][NQ];
+    double p0R[CCAP][NQ];
+    double m3[CCAP][3];
+    // per x-entry, structure of arrays: z(x) = m3 * S_U[c3, x] (rows 0-3),
+    // d(x) = S_U[x,x] - z^T z (rows 4-6), inverse c2-pivot factor m2(x) (rows 7-9).
+    // Before the batches of an item start, the same storage holds Y(x) of the
+    // elimination of U (8 doubles per mode x < c4).
+    double xe[10][XCAP];
+};
+
+// Number of stride classes the children c3 in [2, c4) of one U are split into.
+__host__ __device__ __forceinline__ int n_classes(int c4, uint64_t target) {
+    const uint64_t leaves = binom(c4, 3);
+    uint64_t n = (leaves + target - 1) / target;
+    if (n < 1) n = 1;
+    if (n > (uint64_t)(c4 - 2)) n = (uint64_t)(c4 - 2);
+    return (int)n;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ int c4_max(int M) {
+    return D == 5 ? M - 2 : M - 1;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_t target) {
+    const uint32_t nU = D == 5 ? (uint32_t)(M - 1 - c4) : 1u;
+    return nU * (uint32_t)n_classes(c4, target);
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
+    using SH = TreeShared<D>;
+    constexpr int NP = SH::NP;
+    constexpr int NQ = SH::NQ;
+    constexpr int PALL = NQ - 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH &sh = *reinterpret_cast<SH *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int M = a.M;
+    const int c4hi = c4_max<D>(M);
+    const int K = c4hi - 2;  // c4 runs c4hi, c4hi-1, .., 3
+    double *const slot = a.scratch + (size_t)blockIdx.x * a.slot_doubles;
+    double *const sdiag = slot + 4 * binom2(M);
+    const double *__restrict__ A = a.A;
+
+    // prefix of item counts over c4 in descending order (warp 0, chunked scan)
+    if (tid < 32) {
+        const int per = (K + 31) / 32;
+        const int lo = tid * per, hi = min(K, lo + per);
+        uint32_t sum = 0;
+        for (int k = lo; k < hi; ++k) sum += items_for_c4<D>(M, c4hi - k, target);
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (int k = lo; k < hi; ++k) {
+            sh.c4pref[k] = run;
+            run += items_for_c4<D>(M, c4hi - k, target);
+        }
+        if (tid == 31) sh.c4pref[K] = incl;
+    }
+    __syncthreads();
+    const uint32_t total_items = sh.c4pref[K];
+
+    for (;;) {
+        if (tid == 0) sh.item = atomicAdd(a.counters + D, 1u);
+        __syncthreads();
+        const uint32_t item = sh.item;
+        if (item >= total_items) break;
+        // ---- decode item -> (c4, c5, class s of nc)
+        int lo = 0, hi = K;  // find k with c4pref[k] <= item < c4pref[k+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sh.c4pref[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c4 = c4hi - lo;
+        const int nc = n_classes(c4, target);
+        const uint32_t rr = item - sh.c4pref[lo];
+        const int u = (int)(rr / nc), s = (int)(rr % nc);
+        const int c5 = (D == 5) ? c4 + 1 + u : M;
+
+        // ---- Schur complement of A after eliminating U, modes < c4 -> slot
+        // uniform pivots: m5 = chol(A[c5,c5])^{-1}, y5(c4), m4 = chol(Pi4)^{-1}
+        if (tid == 0) {
+            bool ok = true, ok2 = true;
+            double dd;
+            LInv m5{0, 0, 0};
+            Blk y5c4{0, 0, 0, 0};
+            Sym pi4 = blk_sym(ablk(A, M, c4, c4));
+            if (D == 5) {
+                m5 = chol2_inv(blk_sym(ablk(A, M, c5, c5)), ok, dd);
+                y5c4 = lmul(m5, ablk(A, M, c5, c4));
+                pi4 = sym_sub_gram(pi4, y5c4);
+            }
+            const LInv m4 = chol2_inv(pi4, ok2, dd);
+            if (!ok || !ok2) flag_status(a.status, ST_NOT_POSDEF);
+            sh.upiv[0] = m5.m00; sh.upiv[1] = m5.m10; sh.upiv[2] = m5.m11;
+            sh.upiv[3] = m4.m00; sh.upiv[4] = m4.m10; sh.upiv[5] = m4.m11;
+        }
+        __syncthreads();
+        {
+            // Y(x) = [y5(x); y4(x)] into the x-entry area (it is free until the batches start)
+            double *Y = &sh.xe[0][0];  // 8 doubles per x, x < c4 <= GBS_MAX_MODES: 8*1024 <= 10*XCAP
+            const LInv m5{sh.upiv[0], sh.upiv[1], sh.upiv[2]};
+            const LInv m4{sh.upiv[3], sh.upiv[4], sh.upiv[5]};
+            Blk y5c4{0, 0, 0, 0};
+            if (D == 5) y5c4 = lmul(m5, ablk(A, M, c5, c4));
+            for (int x = tid; x < c4; x += TREE_THREADS) {
+                Blk y5{0, 0, 0, 0};
+                Blk r4 = ablk(A, M, c4, x);
+                if (D == 5) {
+                    y5 = lmul(m5, ablk(A, M, c5, x));
+                    r4 = blk_sub_cross(r4, y5c4, y5);
+                }
+                const Blk y4 = lmul(m4, r4);
+                double *q = Y + 8 * x;
+                q[0] = y5.a00; q[1] = y5.a01; q[2] = y5.a10; q[3] = y5.a11;
+                q[4] = y4.a00; q[5] = y4.a01; q[6] = y4.a10; q[7] = y4.a11;
+            }
+            __syncthreads();
+            const uint32_t npairs = (uint32_t)binom2(c4);
+            for (uint32_t qi = tid; qi < npairs + (uint32_t)c4; qi += TREE_THREADS) {
+                int x, y;
+                if (qi < npairs) pair_decode(qi, x, y);
+                else x = y = (int)(qi - npairs);
+                const double *px = Y + 8 * x, *py = Y + 8 * y;
+                Blk b = ablk(A, M, x, y);
+                const Blk y5x{px[0], px[1], px[2], px[3]}, y5y{py[0], py[1], py[2], py[3]};
+                const Blk y4x{px[4], px[5], px[6], px[7]}, y4y{py[4], py[5], py[6], py[7]};
+                if (D == 5) b = blk_sub_cross(b, y5x, y5y);
+                b = blk_sub_cross(b, y4x, y4y);
+                if (qi < npairs) store_blk(slot + 4 * (size_t)qi, b);
+                else store_blk(sdiag + 4 * (size_t)x, Blk{b.a00, 0.5 * (b.a01 + b.a10), b.a11, 0.0});
+            }
+            __syncthreads();
+        }
+
+        // ---- children c3 = c4-1-s, c4-1-s-nc, ... >= 2, processed in batches
+        const int cfirst = c4 - 1 - s;
+        const int nchild = (cfirst >= 2) ? (cfirst - 2) / nc + 1 : 0;
+        int k0 = 0;
+        while (k0 < nchild) {
+            // batch [k0, k0+nb): identical arithmetic in every thread
+            int nb = 0, xs = 0;
+            while (k0 + nb < nchild && nb < CCAP) {
+                const int c3 = cfirst - (k0 + nb) * nc;
+                if (xs + c3 > XCAP) break;
+                xs += c3;
+                ++nb;
+            }
+            // pre-setup: one thread per child
+            if (tid < nb) {
+                const int b = tid;
+                const int c3 = cfirst - (k0 + b) * nc;
+                int xo = 0;
+                uint32_t lp = 0;
+                for (int q = 0; q < b; ++q) {
+                    const int cq = cfirst - (k0 + q) * nc;
+                    xo += cq;
+                    lp += (uint32_t)binom2(cq);
+                }
+                sh.c3[b] = c3;
+                sh.xoff[b] = xo;
+                sh.lpref[b] = lp;
+                if (b == nb - 1) {
+                    sh.xoff[nb] = xo + c3;
+                    sh.lpref[nb] = lp + (uint32_t)binom2(c3);
+                }
+                int P[3] = {c3, c4, c5};
+                uint64_t idxQ[NQ];
+                child_bases<NP>(P, M, sh.baseJ[b], sh.baseT[b], idxQ);
+                sh.p0R[b][0] = 0.0;
+#pragma unroll
+                for (int q = 1; q < NQ; ++q) sh.p0R[b][q] = a.p0[idxQ[q]];
+                bool ok;
+                double dd;
+                const Sym p3 = Sym{sdiag[4 * c3], sdiag[4 * c3 + 1], sdiag[4 * c3 + 2]};
+                const LInv m3 = chol2_inv(p3, ok, dd);
+                if (!ok) flag_status(a.status, ST_NOT_POSDEF);
+                sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
+            }
+            __syncthreads();
+            // setup: eliminate c3 for every x < c3 of every child in the batch
+            for (int e = tid; e < xs; e += TREE_THREADS) {
+                int lo2 = 0, hi2 = nb;
+                while (hi2 - lo2 > 1) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (sh.xoff[mid] <= e) lo2 = mid;
+                    else hi2 = mid;
+                }
+                const int b = lo2;
+                const int c3 = sh.c3[b];
+                const int x = e - sh.xoff[b];
+                const LInv m3{sh.m3[b][0], sh.m3[b][1], sh.m3[b][2]};
+                const Blk z = lmul(m3, load_blk(slot + 4 * (binom2(c3) + x)));
+                const Sym dx = sym_sub_gram(Sym{sdiag[4 * x], sdiag[4 * x + 1], sdiag[4 * x + 2]}, z);
+                sh.xe[0][e] = z.a00; sh.xe[1][e] = z.a01; sh.xe[2][e] = z.a10; sh.xe[3][e] = z.a11;
+                sh.xe[4][e] = dx.s00; sh.xe[5][e] = dx.s01; sh.xe[6][e] = dx.s11;
+                if (x >= 1) {
+                    bool ok;
+                    double dd;
+                    const LInv m2 = chol2_inv(dx, ok, dd);
+                    if (!ok) flag_status(a.status, ST_NOT_POSDEF);
+                    sh.xe[7][e] = m2.m00; sh.xe[8][e] = m2.m10; sh.xe[9][e] = m2.m11;
+                }
+            }
+            __syncthreads();
+            // leaves (c2, j), j < c2 < c3, flattened over the batch
+            const uint32_t L = sh.lpref[nb];
+            for (uint32_t g = tid; g < L; g += TREE_THREADS) {
+                int lo2 = 0, hi2 = nb;
+                while (hi2 - lo2 > 1) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (sh.lpref[mid] <= g) lo2 = mid;
+                    else hi2 = mid;
+                }
+                const int b = lo2;
+                const uint32_t t = g - sh.lpref[b];
+                int c2, j;
+                pair_decode(t, c2, j);
+                const int xo = sh.xoff[b];
+                const int e2 = xo + c2, ej = xo + j;
+                const Blk z2{sh.xe[0][e2], sh.xe[1][e2], sh.xe[2][e2], sh.xe[3][e2]};
+                const Blk zj{sh.xe[0][ej], sh.xe[1][ej], sh.xe[2][ej], sh.xe[3][ej]};
+                const LInv m2{sh.xe[7][e2], sh.xe[8][e2], sh.xe[9][e2]};
+                const Sym dj{sh.xe[4][ej], sh.xe[5][ej], sh.xe[6][ej]};
+                const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
+                const Sym sch = sym_sub_gram(dj, lmul(m2, X));
+                const double det2 = det_sym(sch);
+                const uint64_t *bJ = sh.baseJ[b];
+                const uint64_t *bT = sh.baseT[b];
+                double P0 = a.p0[bJ[PALL] + c2] * rsqrt(det2);
+                if (!(det2 > 0.0)) {
+                    flag_status(a.status, ST_NOT_POSDEF);
+                    P0 = __longlong_as_double(0x7ff8000000000000ULL);
+                }
+                const double v = combine<NP, MODE>(P0, j, c2, t, bJ, bT, sh.p0R[b], a.p0, a.out);
+                const uint64_t idx = bT[PALL] + t;
+                if (write_p0) a.p0[idx] = P0;
+                if (MODE != MODE_P0) a.out[idx] = v;
+            }
+            __syncthreads();
+            k0 += nb;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(int M, int kmax, int sms) {
+    WsLayout w{};
+    size_t off = 0;
+    w.status_off = off;
+    off = align256(off + 256);
+    w.A_off = off;
+    off = align256(off + sizeof(double) * 4 * (size_t)M * M);
+    w.p0_off = off;
+    const uint64_t np0 = kmax > 1 ? order_offset(M, kmax) : 0;  // orders 1..kmax-1
+    off = align256(off + sizeof(double) * (size_t)np0);
+    w.scratch_off = off;
+    w.slots = sms > 0 ? sms : 1;
+    w.slot_doubles = 4 * ((size_t)binom2(M) + (size_t)M);
+    if (kmax >= 4) off = align256(off + sizeof(double) * w.slot_doubles * w.slots);
+    w.total = off;
+    return w;
+}
+
+template <int D, int MODE>
+static cudaError_t launch_tree(const FwdArgs &a, bool write_p0, cudaStream_t st) {
+    const int M = a.M;
+    const uint64_t leaves = binom(M, D);
+    if (leaves == 0) return cudaSuccess;
+    const int grid_max = a.slots < a.sms ? a.slots : a.sms;
+    uint64_t target = leaves / (2 * (uint64_t)grid_max);
+    if (target < 256) target = 256;
+    uint64_t items = 0;
+    for (int c4 = c4_max<D>(M); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, target);
+    if (items == 0) return cudaSuccess;
+    const int grid = (int)(items < (uint64_t)grid_max ? items : (uint64_t)grid_max);
+    const size_t smem = sizeof(TreeShared<D>);
+    cudaError_t e = cudaFuncSetAttribute(tree_kernel<D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tree_kernel<D, MODE><<<grid, TREE_THREADS, smem, st>>>(a, target, write_p0);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_mode(const FwdArgs &a, cudaStream_t st) {
+    const int M = a.M;
+    auto wp = [&](int d) { return MODE == MODE_P0 || d < a.kmax; };
+    auto mark = [&](int i) {
+        if (a.ev) cudaEventRecord(a.ev[i], st);
+    };
+    cudaError_t e = cudaSuccess;
+    order1_kernel<MODE><<<(M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(a, wp(1));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(2);
+    if (a.kmax >= 2) {
+        const uint64_t n2 = binom2(M);
+        order2_kernel<MODE><<<(unsigned)((n2 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(2));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mark(3);
+    if (a.kmax >= 3) {
+        const uint64_t n3 = binom(M, 3);
+        order3_kernel<MODE><<<(unsigned)((n3 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(3));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mark(4);
+    if (a.kmax >= 4 && (e = launch_tree<4, MODE>(a, wp(4), st)) != cudaSuccess) return e;
+    mark(5);
+    if (a.kmax >= 5 && (e = launch_tree<5, MODE>(a, wp(5), st)) != cudaSuccess) return e;
+    mark(6);
+    return cudaSuccess;
+}
+
+cudaError_t launch_forward(const FwdArgs &a, cudaStream_t st) {
+    const int M = a.M;
+    if (a.ev) cudaEventRecord(a.ev[0], st);
+    pack_kernel<<<(M * M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(a.V, M, a.A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.ev) cudaEventRecord(a.ev[1], st);
+    switch (a.mode) {
+        case MODE_P0: return launch_mode<MODE_P0>(a, st);
+        case MODE_MU: return launch_mode<MODE_MU>(a, st);
+        default: return launch_mode<MODE_KAPPA>(a, st);
+    }
+}
+
+}  // namespace gbs

@@ -1,0 +1,86 @@
+"""The C ABI library loads and exports every entry point include/gbs.h declares;
+host-only helpers (sizes, offsets, colex rank/unrank, argument checks) agree with
+the oracle's enumeration. No kernel is launched. CPU only."""
+import ctypes
+import os
+import re
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2511_14923_gb300 as gbs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    gbs.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gbs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "gbs_cumulants" in names and "gbs_rank" in names
+    L = gbs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_table_size_and_offsets():
+    for M in (1, 2, 5, 8, 50, 144, 1024):
+        for k in range(1, min(M, 5) + 1):
+            assert gbs.table_size(M, k) == sum(comb(M, d) for d in range(1, k + 1))
+            assert gbs.order_offset(M, k) == sum(comb(M, d) for d in range(1, k))
+    assert gbs.table_size(144, 5) == 498685188
+    assert gbs.table_size(0, 1) == 0 and gbs.table_size(4, 5) == 0 and gbs.table_size(10, 6) == 0
+    assert gbs.table_size(1025, 1) == 0
+
+
+@pytest.mark.parametrize("M", [1, 6, 11, 20])
+def test_rank_unrank_match_oracle_enumeration(M):
+    for d in range(1, min(M, 5) + 1):
+        for i, S in enumerate(oracle.enumerate_subsets(M, d)):
+            assert gbs.rank(S) == i
+            assert gbs.unrank(i, d) == list(S)
+
+
+def test_rank_large_modes_bit_exact():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        d = int(rng.integers(1, 6))
+        S = np.sort(rng.choice(1024, d, replace=False))
+        r = gbs.rank(S)
+        assert r == sum(comb(int(c), i + 1) for i, c in enumerate(S))
+        assert gbs.unrank(r, d) == list(S)
+
+
+def test_rank_rejects_bad_input():
+    assert gbs.rank([3, 3]) == 2**64 - 1
+    assert gbs.rank([4, 2]) == 2**64 - 1
+    assert gbs.rank([-1]) == 2**64 - 1
+    with pytest.raises(gbs.GbsError):
+        gbs.unrank(comb(1024, 2), 2)
+
+
+def test_workspace_bytes_rejects_invalid():
+    assert gbs.workspace_bytes(8, 3) > 0
+    assert gbs.lib().gbs_workspace_bytes(8, 9, 0) == 0
+    assert gbs.lib().gbs_workspace_bytes(8, 3, 7) == 0
+
+
+def test_compute_entry_rejects_bad_arguments_without_launching():
+    L = gbs.lib()
+    vp = ctypes.c_void_p
+    # NULL pointers and bad sizes are caught on the host before any CUDA work
+    assert L.gbs_cumulants(vp(0), 8, 3, vp(0), 0, vp(0), 0, vp(0)) == 1
+    assert L.gbs_cumulants(vp(0), 8, 9, vp(0), 0, vp(0), 0, vp(0)) == 1
+    assert L.gbs_vacuum_probs(vp(0), 8, 3, vp(0), 5, vp(0), 0, vp(0)) == 1
+    assert b"kmax" in L.gbs_last_error() or b"precision" in L.gbs_last_error()
