@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
+    p.add_argument("--workload", choices=["m144k5", "m100k5"], default="m144k5",
+                   help="m100k5: smaller case of the same kernels for profiling (not a bench line)")
     return p.parse_args()
 
 
@@ -181,7 +183,11 @@ def main():
     dev = torch.device("cuda", local)
     gbs.build()
 
-    inst = synthetic.config(2)
+    if args.workload == "m144k5":
+        inst = synthetic.config(2)
+    else:
+        inst = synthetic.random_instance(100, 5, seed=20251114 + 100, r_range=(0.8, 1.6), eta_range=(0.3, 0.5),
+                                         n_squeezed=50)
     M, kmax = inst.M, inst.kmax
     N = gbs.table_size(M, kmax)
     prec = args.precision
@@ -269,7 +275,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "subsets/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "M": M, "kmax": kmax, "subsets": N, "precision": prec,
+                "config": {"workload": WORKLOAD if args.workload == "m144k5" else "profiling case M=100 kmax=5", "M": M, "kmax": kmax, "subsets": N, "precision": prec,
                            "table_bytes": N * 8,
                            "l2": "256 MiB buffer written between steps (outside the step events); "
                                  "the 3.99 GB output also exceeds L2",
