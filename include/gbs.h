@@ -131,6 +131,41 @@ int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int prec
 int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
                   void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Size of the fixed scratch array behind gbs_cumulants_noalloc, in MiB. */
+#define GBS_NOALLOC_SCRATCH_MB 64
+
+/* gbs_cumulants for callers that cannot allocate device memory. (The paper has
+   no counterpart; this is a deployment convenience of this library.)
+
+   Who needs it: code that cannot call cudaMalloc where it needs the table --
+   inside an allocator or memory-pool callback, in a plugin whose host
+   application owns every device allocation, or in a runtime that forbids
+   allocation after start-up. Such a caller passes only V (2M x 2M FP64, device)
+   and kappa_out (gbs_table_size(M, kmax) FP64 entries, device); the result
+   equals gbs_cumulants(..., GBS_FP64, ...).
+
+   Scratch: every buffer gbs_cumulants keeps in its workspace lives instead in
+   one file-scope device array of GBS_NOALLOC_SCRATCH_MB MiB, reserved on each
+   GPU that loads the library and held until the process exits. Calls whose
+   workspace (gbs_workspace_bytes) exceeds it are rejected with
+   GBS_ERR_WORKSPACE and a message; on a 152-SM GB300, M = 100 fits with
+   kmax = 5 and M = 144 with kmax <= 4, while M = 144 with kmax = 5 does not.
+   Nothing here calls cudaMalloc, cudaFree or any allocating routine.
+
+   Set-up: the first call on each device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current; make that first call before
+   any stream capture.
+
+   Sharing: all calls in the process share the one array, which keeps the last
+   call's contents (the status word and work counters are cleared at the start
+   of every call). Calls whose work may overlap on the GPU -- on different
+   streams, or from different host threads -- race on the array; serialise
+   them (one stream). Device-side errors leave NaN in the affected entries.
+   Returns GBS_OK, GBS_ERR_INVALID_ARG, GBS_ERR_WORKSPACE or GBS_ERR_CUDA. */
+int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *kappa_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

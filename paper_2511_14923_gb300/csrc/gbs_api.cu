@@ -118,6 +118,12 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
 
 }  // namespace
 
+namespace gbs {
+// Sets the message gbs_last_error() returns on this host thread; for entry
+// points defined in other translation units of the library.
+int record_error(int code, const char *msg) { return code == GBS_OK ? ok() : fail(code, "%s", msg); }
+}  // namespace gbs
+
 extern "C" {
 
 uint64_t gbs_table_size(int M, int kmax) {
