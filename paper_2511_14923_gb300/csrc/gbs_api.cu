@@ -79,8 +79,6 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
     int sms = 0;
     int rc = check_common(V, M, kmax, out, precision, ws, ws_bytes, L, sms);
     if (rc != GBS_OK) return rc;
-    if (precision == GBS_FP32_REFINED)
-        return fail(GBS_ERR_INVALID_ARG, "GBS_FP32_REFINED is not available in this build");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *w = static_cast<char *>(ws);
     cudaError_t e = cudaMemsetAsync(w + L.status_off, 0, 256, st);

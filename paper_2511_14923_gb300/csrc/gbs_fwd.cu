@@ -40,6 +40,7 @@
 #include "gbs.h"
 #include "gbs_common.cuh"
 #include "gbs_fwd.cuh"
+#include "gbs_refined.cuh"
 
 namespace gbs {
 
@@ -222,12 +223,65 @@ struct TreeShared {
     uint64_t baseT[CCAP][NQ];
     double p0R[CCAP][NQ];
     double m3[CCAP][3];
-    // per x-entry, structure of arrays: z(x) = m3 * S_U[c3, x] (rows 0-3),
-    // d(x) = S_U[x,x] - z^T z (rows 4-6), inverse c2-pivot factor m2(x) (rows 7-9).
+    // Per x-entry data, structure of arrays. FP64 path (10 double rows):
+    // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
+    // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (23 float
+    // rows): z hi/lo (0-3, 4-7), d hi/lo (8-10, 11-13), c2 pivot: FP32 factor
+    // l (14-16), its inverse m (17-19), residual d - l l^T (20-22).
     // Before the batches of an item start, the same storage holds Y(x) of the
     // elimination of U (8 doubles per mode x < c4).
-    double xe[10][XCAP];
+    static constexpr int XBYTES = (23 * 4 > 10 * 8 ? 23 * 4 : 10 * 8) * XCAP;
+    alignas(16) unsigned char xraw[XBYTES];
+    __device__ double (*xe())[XCAP] { return reinterpret_cast<double(*)[XCAP]>(xraw); }
+    __device__ float (*xf())[XCAP] { return reinterpret_cast<float(*)[XCAP]>(xraw); }
 };
+
+// Schur-complement slot access. FP64 path: 2x2 blocks as 4 doubles. Refined
+// path: the same 32 bytes hold 4 hi floats then 4 lo floats (value = hi + lo).
+template <int PREC>
+__device__ __forceinline__ Blk slot_pair_f64(const double *slot, size_t q) {
+    if (PREC == 0) return load_blk(slot + 4 * q);
+    const float4 *f = reinterpret_cast<const float4 *>(slot) + 2 * q;
+    const float4 h = f[0], l = f[1];
+    return Blk{join_df(h.x, l.x), join_df(h.y, l.y), join_df(h.z, l.z), join_df(h.w, l.w)};
+}
+template <int PREC>
+__device__ __forceinline__ Sym slot_diag_f64(const double *sdiag, int x) {
+    if (PREC == 0) return Sym{sdiag[4 * x], sdiag[4 * x + 1], sdiag[4 * x + 2]};
+    const float *f = reinterpret_cast<const float *>(sdiag) + 8 * x;
+    return Sym{join_df(f[0], f[3]), join_df(f[1], f[4]), join_df(f[2], f[5])};
+}
+template <int PREC>
+__device__ __forceinline__ void slot_store_pair(double *slot, size_t q, const Blk &b) {
+    if (PREC == 0) {
+        store_blk(slot + 4 * q, b);
+        return;
+    }
+    float4 h, l;
+    split_df(b.a00, h.x, l.x);
+    split_df(b.a01, h.y, l.y);
+    split_df(b.a10, h.z, l.z);
+    split_df(b.a11, h.w, l.w);
+    float4 *f = reinterpret_cast<float4 *>(slot) + 2 * q;
+    f[0] = h;
+    f[1] = l;
+}
+template <int PREC>
+__device__ __forceinline__ void slot_store_diag(double *sdiag, int x, const Sym &d) {
+    if (PREC == 0) {
+        store_blk(sdiag + 4 * (size_t)x, Blk{d.s00, d.s01, d.s11, 0.0});
+        return;
+    }
+    float4 h, l;
+    split_df(d.s00, h.x, h.w);
+    split_df(d.s01, h.y, l.x);
+    split_df(d.s11, h.z, l.y);
+    l.z = l.w = 0.f;
+    // layout: h00 h01 h11 l00 | l01 l11 _ _
+    float4 *f = reinterpret_cast<float4 *>(sdiag) + 2 * (size_t)x;
+    f[0] = h;
+    f[1] = l;
+}
 
 // Number of stride classes the children c3 in [2, c4) of one U are split into.
 __host__ __device__ __forceinline__ int n_classes(int c4, uint64_t target) {
@@ -249,7 +303,7 @@ __host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_
     return nU * (uint32_t)n_classes(c4, target);
 }
 
-template <int D, int MODE>
+template <int D, int MODE, int PREC>
 __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
     using SH = TreeShared<D>;
     constexpr int NP = SH::NP;
@@ -257,6 +311,8 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
     constexpr int PALL = NQ - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
+    double(*const xe)[XCAP] = sh.xe();
+    float(*const xf)[XCAP] = sh.xf();
     const int tid = threadIdx.x;
     const int M = a.M;
     const int c4hi = c4_max<D>(M);
@@ -325,7 +381,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
         __syncthreads();
         {
             // Y(x) = [y5(x); y4(x)] into the x-entry area (it is free until the batches start)
-            double *Y = &sh.xe[0][0];  // 8 doubles per x, x < c4 <= GBS_MAX_MODES: 8*1024 <= 10*XCAP
+            double *Y = &xe[0][0];  // 8 doubles per x, x < c4 <= GBS_MAX_MODES: 8*1024*8 <= XBYTES
             const LInv m5{sh.upiv[0], sh.upiv[1], sh.upiv[2]};
             const LInv m4{sh.upiv[3], sh.upiv[4], sh.upiv[5]};
             Blk y5c4{0, 0, 0, 0};
@@ -354,8 +410,8 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
                 const Blk y4x{px[4], px[5], px[6], px[7]}, y4y{py[4], py[5], py[6], py[7]};
                 if (D == 5) b = blk_sub_cross(b, y5x, y5y);
                 b = blk_sub_cross(b, y4x, y4y);
-                if (qi < npairs) store_blk(slot + 4 * (size_t)qi, b);
-                else store_blk(sdiag + 4 * (size_t)x, Blk{b.a00, 0.5 * (b.a01 + b.a10), b.a11, 0.0});
+                if (qi < npairs) slot_store_pair<PREC>(slot, qi, b);
+                else slot_store_diag<PREC>(sdiag, x, Sym{b.a00, 0.5 * (b.a01 + b.a10), b.a11});
             }
             __syncthreads();
         }
@@ -399,7 +455,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
                 for (int q = 1; q < NQ; ++q) sh.p0R[b][q] = a.p0[idxQ[q]];
                 bool ok;
                 double dd;
-                const Sym p3 = Sym{sdiag[4 * c3], sdiag[4 * c3 + 1], sdiag[4 * c3 + 2]};
+                const Sym p3 = slot_diag_f64<PREC>(sdiag, c3);
                 const LInv m3 = chol2_inv(p3, ok, dd);
                 if (!ok) flag_status(a.status, ST_NOT_POSDEF);
                 sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
@@ -417,16 +473,43 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
                 const int c3 = sh.c3[b];
                 const int x = e - sh.xoff[b];
                 const LInv m3{sh.m3[b][0], sh.m3[b][1], sh.m3[b][2]};
-                const Blk z = lmul(m3, load_blk(slot + 4 * (binom2(c3) + x)));
-                const Sym dx = sym_sub_gram(Sym{sdiag[4 * x], sdiag[4 * x + 1], sdiag[4 * x + 2]}, z);
-                sh.xe[0][e] = z.a00; sh.xe[1][e] = z.a01; sh.xe[2][e] = z.a10; sh.xe[3][e] = z.a11;
-                sh.xe[4][e] = dx.s00; sh.xe[5][e] = dx.s01; sh.xe[6][e] = dx.s11;
-                if (x >= 1) {
-                    bool ok;
-                    double dd;
-                    const LInv m2 = chol2_inv(dx, ok, dd);
-                    if (!ok) flag_status(a.status, ST_NOT_POSDEF);
-                    sh.xe[7][e] = m2.m00; sh.xe[8][e] = m2.m10; sh.xe[9][e] = m2.m11;
+                const Blk z = lmul(m3, slot_pair_f64<PREC>(slot, binom2(c3) + x));
+                const Sym dx = sym_sub_gram(slot_diag_f64<PREC>(sdiag, x), z);
+                if (PREC == 0) {
+                    xe[0][e] = z.a00; xe[1][e] = z.a01; xe[2][e] = z.a10; xe[3][e] = z.a11;
+                    xe[4][e] = dx.s00; xe[5][e] = dx.s01; xe[6][e] = dx.s11;
+                    if (x >= 1) {
+                        bool ok;
+                        double dd;
+                        const LInv m2 = chol2_inv(dx, ok, dd);
+                        if (!ok) flag_status(a.status, ST_NOT_POSDEF);
+                        xe[7][e] = m2.m00; xe[8][e] = m2.m10; xe[9][e] = m2.m11;
+                    }
+                } else {
+                    split_df(z.a00, xf[0][e], xf[4][e]);
+                    split_df(z.a01, xf[1][e], xf[5][e]);
+                    split_df(z.a10, xf[2][e], xf[6][e]);
+                    split_df(z.a11, xf[3][e], xf[7][e]);
+                    split_df(dx.s00, xf[8][e], xf[11][e]);
+                    split_df(dx.s01, xf[9][e], xf[12][e]);
+                    split_df(dx.s11, xf[10][e], xf[13][e]);
+                    if (x >= 1) {
+                        // FP32 Cholesky factor of the c2 pivot d(x), its inverse, and the
+                        // exact residual d - l l^T (FP32 products are exact in FP64)
+                        const float pa = xf[8][e], pb = xf[9][e], pc = xf[10][e];
+                        const float i0 = rsqrtf(pa);
+                        const float l00 = pa * i0, l10 = pb * i0;
+                        const float pq = __fmaf_rn(-l10, l10, pc);
+                        const float i1 = rsqrtf(pq);
+                        const float l11 = pq * i1;
+                        if (!(pa > 0.f) || !(pq > 0.f)) flag_status(a.status, ST_NOT_POSDEF);
+                        xf[14][e] = l00; xf[15][e] = l10; xf[16][e] = l11;
+                        xf[17][e] = i0; xf[18][e] = -l10 * i0 * i1; xf[19][e] = i1;
+                        const double L00 = l00, L10 = l10, L11 = l11;
+                        xf[20][e] = __double2float_rn(fma(-L00, L00, dx.s00));
+                        xf[21][e] = __double2float_rn(fma(-L00, L10, dx.s01));
+                        xf[22][e] = __double2float_rn(fma(-L11, L11, fma(-L10, L10, dx.s11)));
+                    }
                 }
             }
             __syncthreads();
@@ -445,17 +528,33 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
                 pair_decode(t, c2, j);
                 const int xo = sh.xoff[b];
                 const int e2 = xo + c2, ej = xo + j;
-                const Blk z2{sh.xe[0][e2], sh.xe[1][e2], sh.xe[2][e2], sh.xe[3][e2]};
-                const Blk zj{sh.xe[0][ej], sh.xe[1][ej], sh.xe[2][ej], sh.xe[3][ej]};
-                const LInv m2{sh.xe[7][e2], sh.xe[8][e2], sh.xe[9][e2]};
-                const Sym dj{sh.xe[4][ej], sh.xe[5][ej], sh.xe[6][ej]};
-                const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
-                const Sym sch = sym_sub_gram(dj, lmul(m2, X));
-                const double det2 = det_sym(sch);
                 const uint64_t *bJ = sh.baseJ[b];
                 const uint64_t *bT = sh.baseT[b];
-                double P0 = a.p0[bJ[PALL] + c2] * rsqrt(det2);
-                if (!(det2 > 0.0)) {
+                const double P0Sp = a.p0[bJ[PALL] + c2];
+                double P0;
+                bool ok;
+                if (PREC == 0) {
+                    const Blk z2{xe[0][e2], xe[1][e2], xe[2][e2], xe[3][e2]};
+                    const Blk zj{xe[0][ej], xe[1][ej], xe[2][ej], xe[3][ej]};
+                    const LInv m2{xe[7][e2], xe[8][e2], xe[9][e2]};
+                    const Sym dj{xe[4][ej], xe[5][ej], xe[6][ej]};
+                    const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
+                    const Sym sch = sym_sub_gram(dj, lmul(m2, X));
+                    const double det2 = det_sym(sch);
+                    P0 = P0Sp * rsqrt(det2);
+                    ok = det2 > 0.0;
+                } else {
+                    const float4 *fs = reinterpret_cast<const float4 *>(slot) + 2 * (size_t)t;
+                    const float4 sh4 = fs[0], sl4 = fs[1];
+                    const DFBlk S{sh4.x, sh4.y, sh4.z, sh4.w, sl4.x, sl4.y, sl4.z, sl4.w};
+                    const DFBlk z2{xf[0][e2], xf[1][e2], xf[2][e2], xf[3][e2], xf[4][e2], xf[5][e2], xf[6][e2], xf[7][e2]};
+                    const DFBlk zj{xf[0][ej], xf[1][ej], xf[2][ej], xf[3][ej], xf[4][ej], xf[5][ej], xf[6][ej], xf[7][ej]};
+                    const DFSym dj{xf[8][ej], xf[9][ej], xf[10][ej], xf[11][ej], xf[12][ej], xf[13][ej]};
+                    const F32Piv pv{xf[14][e2], xf[15][e2], xf[16][e2], xf[17][e2], xf[18][e2],
+                                    xf[19][e2], xf[20][e2], xf[21][e2], xf[22][e2]};
+                    P0 = refined_leaf_p0(P0Sp, S, z2, zj, dj, pv, ok);
+                }
+                if (!ok) {
                     flag_status(a.status, ST_NOT_POSDEF);
                     P0 = __longlong_as_double(0x7ff8000000000000ULL);
                 }
@@ -492,7 +591,7 @@ WsLayout ws_layout(int M, int kmax, int sms) {
     return w;
 }
 
-template <int D, int MODE>
+template <int D, int MODE, int PREC>
 static cudaError_t launch_tree(const FwdArgs &a, bool write_p0, cudaStream_t st) {
     const int M = a.M;
     const uint64_t leaves = binom(M, D);
@@ -505,9 +604,10 @@ static cudaError_t launch_tree(const FwdArgs &a, bool write_p0, cudaStream_t st)
     if (items == 0) return cudaSuccess;
     const int grid = (int)(items < (uint64_t)grid_max ? items : (uint64_t)grid_max);
     const size_t smem = sizeof(TreeShared<D>);
-    cudaError_t e = cudaFuncSetAttribute(tree_kernel<D, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tree_kernel<D, MODE, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    tree_kernel<D, MODE><<<grid, TREE_THREADS, smem, st>>>(a, target, write_p0);
+    tree_kernel<D, MODE, PREC><<<grid, TREE_THREADS, smem, st>>>(a, target, write_p0);
     return cudaGetLastError();
 }
 
@@ -534,9 +634,15 @@ static cudaError_t launch_mode(const FwdArgs &a, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     mark(4);
-    if (a.kmax >= 4 && (e = launch_tree<4, MODE>(a, wp(4), st)) != cudaSuccess) return e;
+    if (a.kmax >= 4) {
+        e = a.precision == 0 ? launch_tree<4, MODE, 0>(a, wp(4), st) : launch_tree<4, MODE, 1>(a, wp(4), st);
+        if (e != cudaSuccess) return e;
+    }
     mark(5);
-    if (a.kmax >= 5 && (e = launch_tree<5, MODE>(a, wp(5), st)) != cudaSuccess) return e;
+    if (a.kmax >= 5) {
+        e = a.precision == 0 ? launch_tree<5, MODE, 0>(a, wp(5), st) : launch_tree<5, MODE, 1>(a, wp(5), st);
+        if (e != cudaSuccess) return e;
+    }
     mark(6);
     return cudaSuccess;
 }

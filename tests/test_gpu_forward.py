@@ -39,25 +39,28 @@ def assert_tables(got, ref, precision):
         assert err.max() <= tol["abs"], f"{key} max abs err {err.max():.3e} at {err.argmax()}"
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
 @pytest.mark.parametrize("cfg", [0, 1])
-def test_full_tables_match_oracle(cfg):
+def test_full_tables_match_oracle(cfg, precision):
     inst = synthetic.config(cfg)
     ref = oracle.tables(inst.V, inst.kmax)
-    assert_tables(gpu_tables(inst.V, inst.kmax), ref, "fp64")
+    assert_tables(gpu_tables(inst.V, inst.kmax, precision), ref, precision)
 
 
 @pytest.mark.parametrize("M,kmax,seed", [(5, 5, 1), (6, 5, 2), (9, 5, 3), (37, 5, 4), (41, 4, 5), (12, 2, 6),
                                          (1, 1, 7), (2, 2, 8), (3, 3, 9), (4, 4, 10)])
-def test_ragged_sizes_match_oracle(M, kmax, seed):
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_ragged_sizes_match_oracle(M, kmax, seed, precision):
     inst = synthetic.random_instance(M, kmax, seed=seed, r_range=(0.3, 1.4), eta_range=(0.2, 0.8))
     ref = oracle.tables(inst.V, kmax)
-    assert_tables(gpu_tables(inst.V, kmax), ref, "fp64")
+    assert_tables(gpu_tables(inst.V, kmax, precision), ref, precision)
 
 
-def test_config3_full_tables():
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
+def test_config3_full_tables(precision):
     inst = synthetic.config(3)
     ref = oracle.tables(inst.V, inst.kmax)
-    assert_tables(gpu_tables(inst.V, inst.kmax), ref, "fp64")
+    assert_tables(gpu_tables(inst.V, inst.kmax, precision), ref, precision)
 
 
 def test_vacuum_input_gives_trivial_tables():
@@ -127,7 +130,7 @@ def test_workspace_reuse_and_stream_order():
     assert torch.equal(a, c)
 
 
-@pytest.mark.parametrize("precision", ["fp64"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32r"])
 def test_full_size_m144_k5_sampled(precision):
     """The M=144, kmax=5 workload in the configuration the benchmark times: all
     entries of orders <= 3 against the oracle tables, and a seeded sample of
@@ -151,3 +154,15 @@ def test_full_size_m144_k5_sampled(precision):
     # properties that hold at any size: 0 < P0 <= 1, 0 <= mu <= 1
     assert got["p0"].min() > 0 and got["p0"].max() <= 1.0
     assert got["mu"].min() >= -1e-12 and got["mu"].max() <= 1.0
+
+
+def test_refined_path_differs_from_fp64_only_by_rounding():
+    """The refined path is a different computation (FP32 factorisation plus
+    refinement), not a relabelled FP64 run: its order-4/5 entries differ from the
+    FP64 path in the last bits, and stay within the refined tolerance."""
+    inst = synthetic.random_instance(40, 5, seed=77, r_range=(0.8, 1.6), eta_range=(0.3, 0.5))
+    a = gpu_tables(inst.V, 5, "fp64", which=("p0",))["p0"]
+    b = gpu_tables(inst.V, 5, "fp32r", which=("p0",))["p0"]
+    n3 = gbs.table_size(40, 3)
+    assert np.any(a[n3:] != b[n3:])
+    assert np.abs(b / a - 1).max() <= 1e-11
