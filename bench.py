@@ -5,8 +5,12 @@ One step = one gbs_cumulants call that fills all 498,685,188 entries (orders
 r~U[0.8,1.6], Haar U(144), eta_i~U[0.3,0.5]), inputs already in HBM. value =
 subsets/s over the timed steps (device time, CUDA events on the call's stream).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32r]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32r|fp64]
                   [--impl ours|reference]
+
+The headline is the refined-FP32 path (FP32 determinant steps refined to FP64
+accuracy, FP64 sums); the plain FP64 path is timed in the same run and reported
+under "fp64_path".
 
 --impl reference times the CPU oracle (plain FP64 loops, LU determinants and
 explicit partitions) on the host cores, each step a bounded random sample of the
@@ -31,10 +35,13 @@ sys.path.insert(0, ROOT)
 METRIC = "subsets/s and wall time for the order-≤5 M=144 cumulant table, mixed vs FP64 GPU"
 WORKLOAD = ("M=144 kmax=5 click-cumulant table: 72 squeezers r~U[0.8,1.6] on modes 0-71, Haar U(144), "
             "eta_i~U[0.3,0.5], seed 20251116")
-# FP64 flops per order-5 entry of the cumulant table (FMA = 2): 2x2 cross update 16,
-# triangular solve 8, Schur step 12, determinant 3, P0 = P0(S') * det^{-1/2} 3,
-# cumulant recursion 15 FMA = 30.
-FLOPS_PER_LEAF = {"fp64": 72, "fp32r": 72}
+# FP64 flops per order-5 entry of the cumulant table (FMA = 2). FP64 path: 2x2
+# cross update 16, triangular solve 8, Schur step 12, determinant 3,
+# P0 = P0(S') det^{-1/2} 3, cumulant recursion 15 FMA = 30. Refined path: the
+# determinant step runs on the FP32 pipe; FP64 keeps the P0 product (3) and the
+# recursion (30).
+FP64_FLOPS_PER_LEAF = {"fp64": 72, "fp32r": 33}
+DTYPE = {"fp64": "f64", "fp32r": "f32 determinant steps refined to f64 accuracy; f64 sums"}
 FP64_FMA_PER_CLK_PER_SM = 2  # nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz
 
 
@@ -44,7 +51,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", choices=["fp64", "fp32r"], default="fp64")
+    p.add_argument("--precision", choices=["fp64", "fp32r"], default="fp32r",
+                   help="precision of the headline number; the other one is measured too unless --only")
+    p.add_argument("--only", action="store_true", help="measure the headline precision only")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
@@ -151,7 +160,7 @@ def run_reference(args):
     inst = synthetic.config(2)
     import oracle
     oracle.build()
-    per_step = args.cpu_sample or 200000
+    per_step = args.cpu_sample or 1000000
     for w in range(args.warmup):
         time_oracle(inst, per_step // 10, 1000 + w)
     times = [time_oracle(inst, per_step, 2000 + s) for s in range(args.steps)]
@@ -166,6 +175,47 @@ def run_reference(args):
                              "sample": f"{per_step} subsets per step, table order mix"},
             "e2e": {"value": val, "unit": "subsets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure(gbs, torch, V, out, ws, kmax, prec, steps, warmup, flush, stream, dev):
+    """K timed steps of one precision: per-step CUDA events (L2 flushed between
+    steps, outside the events) and per-order kernel times from the library."""
+    def step():
+        gbs.cumulants(V, kmax, prec, out=out, workspace=ws, check=False)
+
+    for _ in range(max(warmup, 0)):
+        step()
+    rc = ws.status()
+    if rc != 0:
+        raise SystemExit(f"device status {rc}: {gbs.lib().gbs_last_error().decode()}")
+    gbs.timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    order_ms = np.zeros(6)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        flush.fill_(float(s))
+        starts[s].record(stream)
+        step()
+        ends[s].record(stream)
+        order_ms += np.array(gbs.timing_read())
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    gbs.timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    return float(sum(step_ms)), order_ms / steps, wall
+
+
+def roofline(prec, M, order_ms, sms, sm_max_mhz):
+    from math import comb
+    t5 = order_ms[5]
+    peak = FP64_FMA_PER_CLK_PER_SM * 2 * sms * sm_max_mhz * 1e6
+    achieved = FP64_FLOPS_PER_LEAF[prec] * comb(M, 5) / (t5 * 1e-3)
+    return {"bound": "alu", "kernel": f"tree_kernel<5, kappa, {prec}> (FP64 pipe)", "achieved": achieved / 1e12,
+            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock (nominal 1.25 TFLOP/s at 2.07 GHz)",
+            "flops_per_entry": FP64_FLOPS_PER_LEAF[prec], "kernel_ms": t5, "order_ms": order_ms.tolist()}
 
 
 def main():
@@ -190,59 +240,34 @@ def main():
                                          n_squeezed=50)
     M, kmax = inst.M, inst.kmax
     N = gbs.table_size(M, kmax)
-    prec = args.precision
+    head = args.precision
+    precs = [head] if args.only else [head] + [p for p in ("fp32r", "fp64") if p != head]
     V = torch.from_numpy(inst.V).to(dev)
     out = torch.empty(N, dtype=torch.float64, device=dev)
-    ws = gbs.Workspace(M, kmax, prec, device=dev)
+    wss = {p: gbs.Workspace(M, kmax, p, device=dev) for p in precs}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    def step():
-        gbs.cumulants(V, kmax, prec, out=out, workspace=ws, check=False)
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    rc = ws.status()
-    if rc != 0:
-        raise SystemExit(f"device status {rc}: {gbs.lib().gbs_last_error().decode()}")
-
-    gbs.timing(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    order_ms = np.zeros(6)
+    res = {}
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler() as clk:
-        t_wall0 = time.perf_counter()
-        for s in range(args.steps):
-            flush.fill_(float(s))                      # L2 flush outside the step's events
-            starts[s].record(stream)
-            step()
-            ends[s].record(stream)
-            order_ms += np.array(gbs.timing_read())    # per-order kernel times of this step
-        torch.cuda.synchronize(dev)
-        t_wall = time.perf_counter() - t_wall0
-    gbs.timing(False)
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    tot_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = N * args.steps * world / (tot_ms * 1e-3)
-
-    # roofline of the dominant kernel (order 5, FP64 pipe)
+        for p in precs:
+            res[p] = measure(gbs, torch, V, out, wss[p], kmax, p, args.steps, args.warmup, flush, stream, dev)
     clocks = clk.summary(local)
-    t5 = order_ms[5] / args.steps
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = FP64_FMA_PER_CLK_PER_SM * 2 * torch.cuda.get_device_properties(dev).multi_processor_count * sm_max * 1e6
-    from math import comb
-    achieved = FLOPS_PER_LEAF[prec] * comb(M, 5) / (t5 * 1e-3)
-    roofline = {"bound": "alu", "kernel": "tree_kernel<5, kappa> (FP64 pipe)", "achieved": achieved / 1e12,
-                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x max SM clock (nominal 1.25 TFLOP/s)",
-                "kernel_ms": t5, "order_ms": [x / args.steps for x in order_ms.tolist()]}
+
+    def total(ms):
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return ms
+
+    tot = {p: total(res[p][0]) for p in precs}
+    value = N * args.steps * world / (tot[head] * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of V, compute, D2H of the table
     e2e = None
@@ -250,9 +275,10 @@ def main():
         hV = torch.from_numpy(inst.V).pin_memory()
         hout = torch.empty(N, dtype=torch.float64).pin_memory()
         dV = torch.empty_like(V)
+        ws = wss[head]
         for _ in range(2):
             dV.copy_(hV, non_blocking=True)
-            gbs.cumulants(dV, kmax, prec, out=out, workspace=ws, check=False)
+            gbs.cumulants(dV, kmax, head, out=out, workspace=ws, check=False)
             hout.copy_(out, non_blocking=True)
         torch.cuda.synchronize(dev)
         n_e2e = max(3, min(args.steps, 5))
@@ -260,7 +286,7 @@ def main():
         e0.record(stream)
         for _ in range(n_e2e):
             dV.copy_(hV, non_blocking=True)
-            gbs.cumulants(dV, kmax, prec, out=out, workspace=ws, check=False)
+            gbs.cumulants(dV, kmax, head, out=out, workspace=ws, check=False)
             hout.copy_(out, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize(dev)
@@ -273,15 +299,19 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             cpu = cpu_baseline(inst, n=args.cpu_sample)
         line = {"metric": METRIC, "value": value, "unit": "subsets/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.workload == "m144k5" else "profiling case M=100 kmax=5", "M": M, "kmax": kmax, "subsets": N, "precision": prec,
-                           "table_bytes": N * 8,
+                "warmup": args.warmup, "ms_per_step": tot[head] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[head], "data": "synthetic",
+                "config": {"workload": WORKLOAD if args.workload == "m144k5" else "profiling case M=100 kmax=5",
+                           "M": M, "kmax": kmax, "subsets": N, "precision": head, "table_bytes": N * 8,
                            "l2": "256 MiB buffer written between steps (outside the step events); "
                                  "the 3.99 GB output also exceeds L2",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "wall_s_timed": t_wall, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 6 * args.steps, "clocks": clocks}
+                "wall_s_timed": res[head][2], "roofline": roofline(head, M, res[head][1], sms, sm_max),
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 6 * args.steps, "clocks": clocks}
+        for p in precs[1:]:
+            line[f"{p}_path"] = {"value": N * args.steps * world / (tot[p] * 1e-3), "unit": "subsets/s",
+                                 "ms_per_step": tot[p] / args.steps, "dtype": DTYPE[p],
+                                 "roofline": roofline(p, M, res[p][1], sms, sm_max)}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
