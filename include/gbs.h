@@ -131,6 +131,40 @@ int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int prec
 int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
                   void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- gradients */
+
+/* Workspace bytes for gbs_cumulants_backward (includes the P0, inverse-moment and
+   P0-gradient tables, 3 x 8 B x gbs_table_size, plus the forward workspace);
+   0 if the arguments are invalid. */
+size_t gbs_backward_workspace_bytes(int M, int kmax);
+
+/* Adjoint of gbs_cumulants (FP64). grad_kappa[gbs_table_size(M,kmax)] = dL/dkt(S)
+   in table layout; grad_V (2M x 2M, row-major, overwritten) receives the
+   symmetric gradient G, dL = sum_ab G[a][b] dV[a][b] for symmetric dV.
+   Chain (derived from Eq. joint_cumulants_def and Eq. vacuum_gaussian_prob):
+   kt(S) = (-1)^{|S|} ky(S) with ky the cumulant of the no-click indicators,
+   whose moments are P0; d ky(S)/d P0(B) = h(S - B) with h the coefficients of
+   1/F(u), F(u) = sum_B P0(B) u^B; dP0(T)/dV_T = -1/2 P0(T) (V_T + I)^{-1}.
+   Device errors (non-positive-definite blocks) go to the workspace status word. */
+int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_kappa, double *grad_V,
+                           void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Covariance of M single-mode squeezed inputs after an interferometer U and
+   per-mode transmissions eta (Eq. ground_truth_cov with hbar = 2 and the lossy
+   transmission matrix diag(sqrt(eta)) U):
+     V = D S Q S^T D + I - D^2,  S = [[Re U, -Im U], [Im U, Re U]],
+     Q = diag(e^{-2 r_1}, .., e^{-2 r_M}, e^{2 r_1}, .., e^{2 r_M}),  D = diag(sqrt(eta), sqrt(eta)).
+   U_re, U_im: M x M row-major; r, eta: length M (eta in (0, 1]); V_out: 2M x 2M.
+   All device pointers. Returns GBS_OK, GBS_ERR_INVALID_ARG or GBS_ERR_CUDA. */
+int gbs_covariance(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
+                   double *V_out, void *cuda_stream);
+
+/* Adjoint of gbs_covariance: given V (its output) and G = dL/dV (2M x 2M),
+   writes grad_r[M] = dL/dr and grad_eta[M] = dL/deta. Device pointers. */
+int gbs_covariance_backward(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
+                            const double *V, const double *grad_V, double *grad_r, double *grad_eta,
+                            void *cuda_stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Size of the fixed scratch array behind gbs_cumulants_noalloc, in MiB. */

@@ -18,7 +18,8 @@ import torch
 
 __all__ = [
     "GbsError", "lib", "build", "table_size", "order_offset", "rank", "unrank", "workspace_bytes",
-    "Workspace", "vacuum_probs", "click_moments", "cumulants", "PRECISIONS",
+    "Workspace", "vacuum_probs", "click_moments", "cumulants", "PRECISIONS", "cumulants_backward",
+    "covariance", "covariance_backward", "CumulantFn", "CovarianceFn", "fit_weights",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -60,6 +61,11 @@ def lib() -> ctypes.CDLL:
     L.gbs_stream_status.argtypes = [vp, vp]; L.gbs_stream_status.restype = i32
     L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
     L.gbs_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float)]; L.gbs_timing_read.restype = i32
+    L.gbs_backward_workspace_bytes.argtypes = [i32, i32]; L.gbs_backward_workspace_bytes.restype = sz
+    L.gbs_cumulants_backward.argtypes = [vp, i32, i32, vp, vp, vp, sz, vp]; L.gbs_cumulants_backward.restype = i32
+    L.gbs_covariance.argtypes = [vp, vp, vp, vp, i32, vp, vp]; L.gbs_covariance.restype = i32
+    L.gbs_covariance_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.gbs_covariance_backward.restype = i32
     for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants"):
         f = getattr(L, name)
         f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
@@ -155,6 +161,95 @@ def click_moments(V, kmax, precision="fp64", out=None, workspace=None, check=Tru
 def cumulants(V, kmax, precision="fp64", out=None, workspace=None, check=True):
     """Joint click cumulants kt(S) for every 1 <= |S| <= kmax."""
     return _forward("gbs_cumulants", V, kmax, precision, out, workspace, check)
+
+
+def _vp(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev64(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    return t.contiguous()
+
+
+def cumulants_backward(V, kmax, grad_kappa, workspace: torch.Tensor | None = None, check=True):
+    """dL/dV (2M x 2M, symmetric) from dL/dkt (table layout), FP64."""
+    V, M = _prep(V)
+    g = _dev64(grad_kappa, "grad_kappa")
+    n = table_size(M, kmax)
+    if g.numel() != n:
+        raise ValueError(f"grad_kappa must have {n} entries")
+    nb = int(lib().gbs_backward_workspace_bytes(M, kmax))
+    ws = workspace if workspace is not None else torch.empty(nb, dtype=torch.uint8, device=V.device)
+    out = torch.empty_like(V)
+    st = torch.cuda.current_stream(V.device)
+    _check(lib().gbs_cumulants_backward(_vp(V), M, kmax, _vp(g), _vp(out), _vp(ws), ws.numel(),
+                                        ctypes.c_void_p(st.cuda_stream)))
+    if check:
+        _check(lib().gbs_stream_status(_vp(ws), ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def covariance(U: torch.Tensor, r: torch.Tensor, eta: torch.Tensor) -> torch.Tensor:
+    """V = D S Q S^T D + I - D^2 for squeezers r, interferometer U (complex M x M)
+    and per-mode transmissions eta (all CUDA tensors)."""
+    Ur, Ui = U.real.to(torch.float64).contiguous(), U.imag.to(torch.float64).contiguous()
+    r, eta = _dev64(r, "r"), _dev64(eta, "eta")
+    M = Ur.shape[0]
+    V = torch.empty(2 * M, 2 * M, dtype=torch.float64, device=r.device)
+    st = torch.cuda.current_stream(r.device)
+    _check(lib().gbs_covariance(_vp(Ur), _vp(Ui), _vp(r), _vp(eta), M, _vp(V), ctypes.c_void_p(st.cuda_stream)))
+    return V
+
+
+def covariance_backward(U, r, eta, V, grad_V):
+    Ur, Ui = U.real.to(torch.float64).contiguous(), U.imag.to(torch.float64).contiguous()
+    r, eta, V, G = _dev64(r, "r"), _dev64(eta, "eta"), _dev64(V, "V"), _dev64(grad_V, "grad_V")
+    M = Ur.shape[0]
+    dr, de = torch.empty_like(r), torch.empty_like(eta)
+    st = torch.cuda.current_stream(r.device)
+    _check(lib().gbs_covariance_backward(_vp(Ur), _vp(Ui), _vp(r), _vp(eta), M, _vp(V), _vp(G), _vp(dr), _vp(de),
+                                         ctypes.c_void_p(st.cuda_stream)))
+    return dr, de
+
+
+class CumulantFn(torch.autograd.Function):
+    """kt = cumulants(V); backward through gbs_cumulants_backward."""
+
+    @staticmethod
+    def forward(ctx, V, kmax, precision="fp64"):
+        ctx.save_for_backward(V)
+        ctx.kmax = kmax
+        return cumulants(V, kmax, precision)
+
+    @staticmethod
+    def backward(ctx, g):
+        (V,) = ctx.saved_tensors
+        return cumulants_backward(V, ctx.kmax, g.contiguous()), None, None
+
+
+class CovarianceFn(torch.autograd.Function):
+    """V = covariance(U, r, eta); gradients flow to r and eta (U is fixed)."""
+
+    @staticmethod
+    def forward(ctx, r, eta, U):
+        V = covariance(U, r, eta)
+        ctx.save_for_backward(r, eta, V)
+        ctx.U = U
+        return V
+
+    @staticmethod
+    def backward(ctx, G):
+        r, eta, V = ctx.saved_tensors
+        dr, de = covariance_backward(ctx.U, r, eta, V, G.contiguous())
+        return dr, de, None
+
+
+def fit_weights(M: int, kmax: int, device=None) -> torch.Tensor:
+    """Per-entry loss weights 1 / C(M, d) (each order weighs the same in total)."""
+    return torch.cat([torch.full((comb(M, d),), 1.0 / comb(M, d), dtype=torch.float64, device=device)
+                      for d in range(1, kmax + 1)])
 
 
 def timing(on: bool) -> None:

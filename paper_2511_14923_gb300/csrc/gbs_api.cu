@@ -7,6 +7,7 @@
 #include "gbs.h"
 #include "gbs_common.cuh"
 #include "gbs_fwd.cuh"
+#include "gbs_bwd.cuh"
 
 namespace {
 
@@ -200,6 +201,85 @@ int gbs_stream_status(const void *workspace, void *cuda_stream) {
     if (s & gbs::ST_NOT_POSDEF)
         return fail(GBS_ERR_NOT_POSDEF, "a reduced covariance (V_T + I)/2 is not positive definite");
     if (s & gbs::ST_BAD_INDEX) return fail(GBS_ERR_INVALID_ARG, "a device index check failed");
+    return ok();
+}
+
+size_t gbs_backward_workspace_bytes(int M, int kmax) {
+    if (!valid_mk(M, kmax)) return 0;
+    const int sms = device_sms();
+    return gbs::bwd_layout(M, kmax, sms > 0 ? sms : 1).total;
+}
+
+int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_kappa, double *grad_V,
+                           void *workspace, size_t ws_bytes, void *cuda_stream) {
+    if (!valid_mk(M, kmax))
+        return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d and 1 <= kmax <= min(M, %d); got M=%d kmax=%d",
+                    GBS_MAX_MODES, GBS_MAX_ORDER, M, kmax);
+    if (!V || !grad_kappa || !grad_V || !workspace)
+        return fail(GBS_ERR_INVALID_ARG, "V, grad_kappa, grad_V and workspace must be non-NULL");
+    if (((uintptr_t)V & 7) || ((uintptr_t)grad_kappa & 7) || ((uintptr_t)grad_V & 7) || ((uintptr_t)workspace & 255))
+        return fail(GBS_ERR_INVALID_ARG, "arrays must be 8-byte aligned and the workspace 256-byte aligned");
+    if (!is_device_ptr(V) || !is_device_ptr(grad_kappa) || !is_device_ptr(grad_V) || !is_device_ptr(workspace))
+        return fail(GBS_ERR_INVALID_ARG, "all arrays must be CUDA device (or managed) memory");
+    const int sms = device_sms();
+    if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
+    const gbs::BwdLayout L = gbs::bwd_layout(M, kmax, sms);
+    if (ws_bytes < L.total)
+        return fail(GBS_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.total);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    char *w = static_cast<char *>(workspace);
+    cudaError_t e = cudaMemsetAsync(w + L.fwd.status_off, 0, 256, st);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    gbs::BwdArgs b{};
+    b.M = M;
+    b.kmax = kmax;
+    gbs::FwdArgs &a = b.fwd;
+    a.V = V;
+    a.M = M;
+    a.kmax = kmax;
+    a.mode = gbs::MODE_P0;
+    a.precision = GBS_FP64;
+    a.A = reinterpret_cast<double *>(w + L.fwd.A_off);
+    a.status = reinterpret_cast<unsigned *>(w + L.fwd.status_off);
+    a.counters = a.status + 8;
+    a.scratch = reinterpret_cast<double *>(w + L.fwd.scratch_off);
+    a.slot_doubles = L.fwd.slot_doubles;
+    a.slots = L.fwd.slots;
+    a.sms = sms;
+    a.ev = nullptr;
+    b.gk = grad_kappa;
+    b.gV = grad_V;
+    b.p0 = reinterpret_cast<double *>(w + L.p0_off);
+    b.h = reinterpret_cast<double *>(w + L.h_off);
+    b.gp0 = reinterpret_cast<double *>(w + L.gp0_off);
+    e = gbs::launch_backward(b, st);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int gbs_covariance(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
+                   double *V_out, void *cuda_stream) {
+    if (M < 1 || M > GBS_MAX_MODES) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES);
+    const void *ptrs[] = {U_re, U_im, r, eta, V_out};
+    for (const void *p : ptrs)
+        if (!p || ((uintptr_t)p & 7) || !is_device_ptr(p))
+            return fail(GBS_ERR_INVALID_ARG, "all arrays must be non-NULL, 8-byte aligned device memory");
+    cudaError_t e = gbs::launch_covariance(U_re, U_im, r, eta, M, V_out, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int gbs_covariance_backward(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
+                            const double *V, const double *grad_V, double *grad_r, double *grad_eta,
+                            void *cuda_stream) {
+    if (M < 1 || M > GBS_MAX_MODES) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES);
+    const void *ptrs[] = {U_re, U_im, r, eta, V, grad_V, grad_r, grad_eta};
+    for (const void *p : ptrs)
+        if (!p || ((uintptr_t)p & 7) || !is_device_ptr(p))
+            return fail(GBS_ERR_INVALID_ARG, "all arrays must be non-NULL, 8-byte aligned device memory");
+    cudaError_t e = gbs::launch_covariance_bwd(U_re, U_im, r, eta, M, V, grad_V, grad_r, grad_eta,
+                                               static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     return ok();
 }
 
