@@ -131,6 +131,40 @@ int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int prec
 int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
                   void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- ragged batches */
+
+/* One instance of a batch: its covariance V (2M x 2M, device) and the output
+   kappa_out (gbs_table_size(M, kmax) FP64 entries, device; outputs of different
+   instances must not overlap). */
+typedef struct {
+    const double *V;
+    double *kappa_out;
+    int M;
+    int kmax;
+} gbs_instance;
+
+/* Workspace bytes for a batch described by the HOST array inst[0..n). */
+size_t gbs_batched_workspace_bytes(const gbs_instance *inst, int n, int precision);
+
+/* Writes the batch plan into the workspace: instance order (largest M first),
+   per-instance packing buffers and lower-order P0 tables, per-phase work prefix
+   sums, and the prefix-tree item tables. inst is a HOST array; the pointers in it
+   are device pointers that must stay valid while the plan is used. Copies the
+   plan with a host-to-device copy and synchronises cuda_stream: call it outside
+   any stream capture. Returns GBS_OK, GBS_ERR_INVALID_ARG, GBS_ERR_WORKSPACE or
+   GBS_ERR_CUDA. */
+int gbs_batched_plan(const gbs_instance *inst, int n, int precision, void *workspace, size_t ws_bytes,
+                     void *cuda_stream);
+
+/* Click-cumulant tables of every instance of the planned batch in ONE persistent
+   cooperative kernel launch (phases: packing, orders 1-3, order 4, order 5,
+   separated by grid-wide barriers; prefix-tree items of all instances share one
+   queue per order). Reads V from the device pointers recorded by the plan, so it
+   may be captured in a CUDA graph and replayed after V changes in place.
+   precision must equal the plan's. Asynchronous; device errors go to the status
+   word (gbs_stream_status). */
+int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream);
+
 /* ---------------------------------------------------------------- gradients */
 
 /* Workspace bytes for gbs_cumulants_backward (includes the P0, inverse-moment and

@@ -19,7 +19,7 @@ import torch
 __all__ = [
     "GbsError", "lib", "build", "table_size", "order_offset", "rank", "unrank", "workspace_bytes",
     "Workspace", "vacuum_probs", "click_moments", "cumulants", "PRECISIONS", "cumulants_backward",
-    "covariance", "covariance_backward", "CumulantFn", "CovarianceFn", "fit_weights",
+    "covariance", "covariance_backward", "CumulantFn", "CovarianceFn", "fit_weights", "Batch",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,6 +40,10 @@ class GbsError(RuntimeError):
 def build(force: bool = False) -> str:
     from . import _build
     return _build.build(force=force)
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_void_p), ("kappa_out", ctypes.c_void_p), ("M", ctypes.c_int), ("kmax", ctypes.c_int)]
 
 
 def lib() -> ctypes.CDLL:
@@ -66,6 +70,10 @@ def lib() -> ctypes.CDLL:
     L.gbs_covariance.argtypes = [vp, vp, vp, vp, i32, vp, vp]; L.gbs_covariance.restype = i32
     L.gbs_covariance_backward.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp]
     L.gbs_covariance_backward.restype = i32
+    L.gbs_batched_workspace_bytes.argtypes = [ctypes.POINTER(_Instance), i32, i32]
+    L.gbs_batched_workspace_bytes.restype = sz
+    L.gbs_batched_plan.argtypes = [ctypes.POINTER(_Instance), i32, i32, vp, sz, vp]; L.gbs_batched_plan.restype = i32
+    L.gbs_cumulants_batched.argtypes = [i32, vp, vp]; L.gbs_cumulants_batched.restype = i32
     for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants"):
         f = getattr(L, name)
         f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
@@ -250,6 +258,69 @@ def fit_weights(M: int, kmax: int, device=None) -> torch.Tensor:
     """Per-entry loss weights 1 / C(M, d) (each order weighs the same in total)."""
     return torch.cat([torch.full((comb(M, d),), 1.0 / comb(M, d), dtype=torch.float64, device=device)
                       for d in range(1, kmax + 1)])
+
+
+class Batch:
+    """Ragged batch of click-cumulant tables computed by one persistent launch.
+
+    Vs: list of CUDA float64 2M x 2M covariances (kept by reference: update them
+    in place and call run() again, or replay the captured graph); kmaxes: list of
+    orders. outputs[i] receives instance i's table."""
+
+    def __init__(self, Vs, kmaxes, precision="fp32r"):
+        self.Vs = [_prep(V)[0] for V in Vs]
+        self.kmaxes = [int(k) for k in kmaxes]
+        self.precision = precision
+        dev = self.Vs[0].device
+        self.outputs = []
+        arr = (_Instance * len(self.Vs))()
+        for i, (V, k) in enumerate(zip(self.Vs, self.kmaxes)):
+            M = V.shape[0] // 2
+            n = table_size(M, k)
+            if n == 0:
+                raise GbsError(1, f"instance {i}: invalid (M={M}, kmax={k})")
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+            self.outputs.append(out)
+            arr[i] = _Instance(V.data_ptr(), out.data_ptr(), M, k)
+        self._arr = arr
+        nb = int(lib().gbs_batched_workspace_bytes(arr, len(arr), PRECISIONS[precision]))
+        if nb == 0:
+            raise GbsError(1, lib().gbs_last_error().decode())
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        st = torch.cuda.current_stream(dev)
+        _check(lib().gbs_batched_plan(arr, len(arr), PRECISIONS[precision], _vp(self.ws), nb,
+                                      ctypes.c_void_p(st.cuda_stream)))
+        self.graph = None
+
+    def run(self, check=False):
+        st = torch.cuda.current_stream(self.ws.device)
+        _check(lib().gbs_cumulants_batched(PRECISIONS[self.precision], _vp(self.ws), ctypes.c_void_p(st.cuda_stream)))
+        if check:
+            _check(lib().gbs_stream_status(_vp(self.ws), ctypes.c_void_p(st.cuda_stream)))
+        return self.outputs
+
+    def capture(self):
+        """Capture run() in a CUDA graph (after one eager warm-up run)."""
+        self.run()
+        torch.cuda.synchronize(self.ws.device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.ws.device)
+        s.wait_stream(torch.cuda.current_stream(self.ws.device))
+        with torch.cuda.stream(s):
+            g.capture_begin()
+            self.run()
+            g.capture_end()
+        torch.cuda.current_stream(self.ws.device).wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs
+
+    def status(self):
+        st = torch.cuda.current_stream(self.ws.device)
+        return int(lib().gbs_stream_status(_vp(self.ws), ctypes.c_void_p(st.cuda_stream)))
 
 
 def timing(on: bool) -> None:

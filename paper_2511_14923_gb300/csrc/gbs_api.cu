@@ -8,6 +8,7 @@
 #include "gbs_common.cuh"
 #include "gbs_fwd.cuh"
 #include "gbs_bwd.cuh"
+#include "gbs_batch.cuh"
 
 namespace {
 
@@ -254,6 +255,59 @@ int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_
     b.gp0 = reinterpret_cast<double *>(w + L.gp0_off);
     e = gbs::launch_backward(b, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+static int check_batch(const gbs_instance *inst, int n, int precision) {
+    if (!inst || n < 1 || n > (1 << 20)) return fail(GBS_ERR_INVALID_ARG, "need a host array of 1..2^20 instances");
+    if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
+        return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
+    for (int i = 0; i < n; ++i) {
+        if (!valid_mk(inst[i].M, inst[i].kmax))
+            return fail(GBS_ERR_INVALID_ARG, "instance %d: need 1 <= M <= %d and 1 <= kmax <= min(M, %d)", i,
+                        GBS_MAX_MODES, GBS_MAX_ORDER);
+        if (!inst[i].V || !inst[i].kappa_out || ((uintptr_t)inst[i].V & 7) || ((uintptr_t)inst[i].kappa_out & 7))
+            return fail(GBS_ERR_INVALID_ARG, "instance %d: V and kappa_out must be non-NULL and 8-byte aligned", i);
+    }
+    return GBS_OK;
+}
+
+size_t gbs_batched_workspace_bytes(const gbs_instance *inst, int n, int precision) {
+    if (check_batch(inst, n, precision) != GBS_OK) return 0;
+    const int sms = device_sms();
+    return gbs::batched_workspace_bytes(inst, n, precision, sms > 0 ? sms : 1);
+}
+
+int gbs_batched_plan(const gbs_instance *inst, int n, int precision, void *workspace, size_t ws_bytes,
+                     void *cuda_stream) {
+    int rc = check_batch(inst, n, precision);
+    if (rc != GBS_OK) return rc;
+    if (!workspace || ((uintptr_t)workspace & 255) || !is_device_ptr(workspace))
+        return fail(GBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned device memory");
+    for (int i = 0; i < n; ++i)
+        if (!is_device_ptr(inst[i].V) || !is_device_ptr(inst[i].kappa_out))
+            return fail(GBS_ERR_INVALID_ARG, "instance %d: V and kappa_out must be device memory", i);
+    const int sms = device_sms();
+    if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
+    size_t needed = 0;
+    rc = gbs::batched_plan(inst, n, precision, static_cast<char *>(workspace), ws_bytes, sms,
+                           static_cast<cudaStream_t>(cuda_stream), needed);
+    if (rc == GBS_ERR_WORKSPACE)
+        return fail(rc, "workspace too small: %zu bytes given, %zu needed", ws_bytes, needed);
+    if (rc != GBS_OK) return fail(rc, "copying the batch plan failed");
+    return ok();
+}
+
+int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream) {
+    if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
+        return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(GBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned device memory");
+    const int sms = device_sms();
+    if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
+    cudaError_t e = gbs::launch_batched(static_cast<char *>(workspace), precision, sms,
+                                        static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
     return ok();
 }
 

@@ -37,289 +37,43 @@
 //                   one 2x2 triangular solve and one 2x2 Schur step.
 #include <cstdio>
 
-#include "gbs.h"
-#include "gbs_common.cuh"
-#include "gbs_fwd.cuh"
-#include "gbs_refined.cuh"
+#include "gbs_tree.cuh"
 
 namespace gbs {
 
-constexpr int FLAT_THREADS = 256;
-constexpr int TREE_THREADS = 512;
-constexpr int XCAP = 1152;  // per-batch x-entries in shared memory (>= GBS_MAX_MODES)
-constexpr int CCAP = 64;    // per-batch children
-
-// ---------------------------------------------------------------- shared combine step
-
-// Per-child constants of the gathers. P = {c_3, .., c_D} ascending, NP = D-2
-// elements, subsets of P by bitmask over P's positions.
-//   baseJ[Q]: table index of {x} + Q is baseJ[Q] + x   (x < min P)
-//   baseT[Q]: table index of {j, c2} + Q is baseT[Q] + t, t = C(c2,2) + j
-//   idxQ[Q] : table index of Q (Q nonempty)
-template <int NP>
-__device__ __forceinline__ void child_bases(const int *P, int M, uint64_t *baseJ, uint64_t *baseT, uint64_t *idxQ) {
-    uint64_t off[GBS_MAX_ORDER + 2];
-    off[0] = 0;
-    off[1] = 0;
-    for (int m = 2; m <= NP + 2; ++m) off[m] = off[m - 1] + binom(M, m - 1);
-#pragma unroll
-    for (int q = 0; q < (1 << NP); ++q) {
-        int m = __popc(q);
-        uint64_t sJ = off[m + 1], sT = off[m + 2], sQ = off[m];
-        int i = 0;
-#pragma unroll
-        for (int e = 0; e < NP; ++e)
-            if (q >> e & 1) {
-                ++i;
-                sJ += binom(P[e], i + 1);
-                sT += binom(P[e], i + 2);
-                sQ += binom(P[e], i);
-            }
-        baseJ[q] = sJ;
-        baseT[q] = sT;
-        idxQ[q] = sQ;
-    }
-}
-
-// Mode-specific value of the leaf S = {j, c2} + P (|P| = NP) given P0(S).
-// p0R[R] = P0(R) for nonempty R subset of P.
-template <int NP, int MODE>
-__device__ __forceinline__ double combine(double P0S, int j, int c2, uint32_t t, const uint64_t *baseJ,
-                                          const uint64_t *baseT, const double *p0R, const double *__restrict__ p0tab,
-                                          const double *__restrict__ outtab) {
-    constexpr int PALL = (1 << NP) - 1;
-    if (MODE == MODE_P0) return P0S;
-    if (MODE == MODE_MU) {
-        double acc = outtab[baseJ[PALL] + c2];  // mu(S')
-#pragma unroll
-        for (int q = 0; q <= PALL; ++q) {
-            const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
-            acc = fma(-sg, p0tab[baseJ[q] + j], acc);
-            const double t2 = (q == PALL) ? P0S : p0tab[baseT[q] + t];
-            acc = fma(sg, t2, acc);
-        }
-        return acc;
-    }
-    // MODE_KAPPA
-    double acc = fma(-p0tab[j], p0tab[baseJ[PALL] + c2], P0S);
-#pragma unroll
-    for (int q = 1; q <= PALL; ++q) {
-        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
-        acc = fma(sg * outtab[baseJ[q] + j], p0tab[baseJ[PALL ^ q] + c2], acc);
-    }
-#pragma unroll
-    for (int q = 0; q < PALL; ++q) {
-        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
-        acc = fma(-sg * outtab[baseT[q] + t], p0R[PALL ^ q], acc);
-    }
-    return ((NP + 2) & 1) ? -acc : acc;
-}
-
-// ---------------------------------------------------------------- small kernels
-
 __global__ void pack_kernel(const double *__restrict__ V, int M, double *__restrict__ A) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * M) return;
-    const int x = idx / M, y = idx - x * M;
-    const size_t n2 = 2 * (size_t)M;
-    double a00 = V[x * n2 + y], a01 = V[x * n2 + y + M];
-    double a10 = V[(x + M) * n2 + y], a11 = V[(x + M) * n2 + y + M];
-    if (x == y) {
-        a00 += 1.0;
-        a11 += 1.0;
-    }
-    store_blk(A + 4 * (size_t)idx, Blk{0.5 * a00, 0.5 * a01, 0.5 * a10, 0.5 * a11});
+    if (idx < M * M) pack_entry(V, M, A, idx);
 }
 
 template <int MODE>
 __global__ void order1_kernel(FwdArgs a, bool write_p0) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.M) return;
-    const Sym s = blk_sym(ablk(a.A, a.M, j, j));
-    const double det = det_sym(s);
-    double P0 = rsqrt(det);
-    if (!(det > 0.0) || !(s.s00 > 0.0)) {
-        flag_status(a.status, ST_NOT_POSDEF);
-        P0 = __longlong_as_double(0x7ff8000000000000ULL);
-    }
-    if (write_p0) a.p0[j] = P0;
-    if (MODE != MODE_P0) a.out[j] = 1.0 - P0;  // mu({j}) = kt({j}) = 1 - P0({j})
+    if (j < a.M) order1_entry<MODE>(a, j, write_p0);
 }
 
 template <int MODE>
 __global__ void order2_kernel(FwdArgs a, bool write_p0) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int M = a.M;
-    if (t >= binom2(M)) return;
-    int c2, j;
-    pair_decode(t, c2, j);
-    bool ok;
-    double detp;
-    const LInv m2 = chol2_inv(blk_sym(ablk(a.A, M, c2, c2)), ok, detp);
-    const Blk w = lmul(m2, ablk(a.A, M, c2, j));
-    const Sym sch = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), w);
-    const double det2 = det_sym(sch);
-    double P0 = a.p0[c2] * rsqrt(det2);
-    if (!(det2 > 0.0) || !ok) {
-        flag_status(a.status, ST_NOT_POSDEF);
-        P0 = __longlong_as_double(0x7ff8000000000000ULL);
-    }
-    const uint64_t idx = (uint64_t)M + t;
-    if (write_p0) a.p0[idx] = P0;
-    if (MODE == MODE_MU) a.out[idx] = a.out[c2] - a.p0[j] + P0;
-    if (MODE == MODE_KAPPA) a.out[idx] = fma(-a.p0[j], a.p0[c2], P0);
+    if (t < binom2(a.M)) order2_entry<MODE>(a, t, write_p0);
 }
 
 template <int MODE>
 __global__ void order3_kernel(FwdArgs a, bool write_p0) {
     const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int M = a.M;
-    if (r >= binom(M, 3)) return;
-    int s[3];
-    colex_unrank(r, 3, s);
-    const int j = s[0], c2 = s[1], c3 = s[2];
-    const uint32_t t = (uint32_t)binom2(c2) + j;
-    bool ok3, ok2;
-    double dd;
-    const LInv m3 = chol2_inv(blk_sym(ablk(a.A, M, c3, c3)), ok3, dd);
-    const Blk z2 = lmul(m3, ablk(a.A, M, c3, c2));
-    const Blk zj = lmul(m3, ablk(a.A, M, c3, j));
-    const LInv m2 = chol2_inv(sym_sub_gram(blk_sym(ablk(a.A, M, c2, c2)), z2), ok2, dd);
-    const Sym dj = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), zj);
-    const Blk X = blk_sub_cross(ablk(a.A, M, c2, j), z2, zj);
-    const Sym sch = sym_sub_gram(dj, lmul(m2, X));
-    const double det2 = det_sym(sch);
-    uint64_t baseJ[2], baseT[2], idxQ[2];
-    const int P[1] = {c3};
-    child_bases<1>(P, M, baseJ, baseT, idxQ);
-    double P0 = a.p0[baseJ[1] + c2] * rsqrt(det2);
-    if (!(det2 > 0.0) || !ok3 || !ok2) {
-        flag_status(a.status, ST_NOT_POSDEF);
-        P0 = __longlong_as_double(0x7ff8000000000000ULL);
-    }
-    const double p0R[2] = {0.0, a.p0[idxQ[1]]};
-    const double v = combine<1, MODE>(P0, j, c2, t, baseJ, baseT, p0R, a.p0, a.out);
-    const uint64_t idx = baseT[1] + t;
-    if (write_p0) a.p0[idx] = P0;
-    if (MODE != MODE_P0) a.out[idx] = v;
-}
-
-// ---------------------------------------------------------------- tree kernel
-
-template <int D>
-struct TreeShared {
-    static constexpr int NP = D - 2;       // |P|
-    static constexpr int NQ = 1 << NP;     // subsets of P
-    // item decode
-    uint32_t c4pref[GBS_MAX_MODES + 2];
-    uint32_t item;
-    // uniform pivots of the item's U
-    double upiv[8];
-    // children of the current batch
-    int c3[CCAP];
-    int xoff[CCAP + 1];
-    uint32_t lpref[CCAP + 1];
-    uint64_t baseJ[CCAP][NQ];
-    uint64_t baseT[CCAP][NQ];
-    double p0R[CCAP][NQ];
-    double m3[CCAP][3];
-    // Per x-entry data, structure of arrays. FP64 path (10 double rows):
-    // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
-    // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (23 float
-    // rows): z hi/lo (0-3, 4-7), d hi/lo (8-10, 11-13), c2 pivot: FP32 factor
-    // l (14-16), its inverse m (17-19), residual d - l l^T (20-22).
-    // Before the batches of an item start, the same storage holds Y(x) of the
-    // elimination of U (8 doubles per mode x < c4).
-    static constexpr int XBYTES = (23 * 4 > 10 * 8 ? 23 * 4 : 10 * 8) * XCAP;
-    alignas(16) unsigned char xraw[XBYTES];
-    __device__ double (*xe())[XCAP] { return reinterpret_cast<double(*)[XCAP]>(xraw); }
-    __device__ float (*xf())[XCAP] { return reinterpret_cast<float(*)[XCAP]>(xraw); }
-};
-
-// Schur-complement slot access. FP64 path: 2x2 blocks as 4 doubles. Refined
-// path: the same 32 bytes hold 4 hi floats then 4 lo floats (value = hi + lo).
-template <int PREC>
-__device__ __forceinline__ Blk slot_pair_f64(const double *slot, size_t q) {
-    if (PREC == 0) return load_blk(slot + 4 * q);
-    const float4 *f = reinterpret_cast<const float4 *>(slot) + 2 * q;
-    const float4 h = f[0], l = f[1];
-    return Blk{join_df(h.x, l.x), join_df(h.y, l.y), join_df(h.z, l.z), join_df(h.w, l.w)};
-}
-template <int PREC>
-__device__ __forceinline__ Sym slot_diag_f64(const double *sdiag, int x) {
-    if (PREC == 0) return Sym{sdiag[4 * x], sdiag[4 * x + 1], sdiag[4 * x + 2]};
-    const float *f = reinterpret_cast<const float *>(sdiag) + 8 * x;
-    return Sym{join_df(f[0], f[3]), join_df(f[1], f[4]), join_df(f[2], f[5])};
-}
-template <int PREC>
-__device__ __forceinline__ void slot_store_pair(double *slot, size_t q, const Blk &b) {
-    if (PREC == 0) {
-        store_blk(slot + 4 * q, b);
-        return;
-    }
-    float4 h, l;
-    split_df(b.a00, h.x, l.x);
-    split_df(b.a01, h.y, l.y);
-    split_df(b.a10, h.z, l.z);
-    split_df(b.a11, h.w, l.w);
-    float4 *f = reinterpret_cast<float4 *>(slot) + 2 * q;
-    f[0] = h;
-    f[1] = l;
-}
-template <int PREC>
-__device__ __forceinline__ void slot_store_diag(double *sdiag, int x, const Sym &d) {
-    if (PREC == 0) {
-        store_blk(sdiag + 4 * (size_t)x, Blk{d.s00, d.s01, d.s11, 0.0});
-        return;
-    }
-    float4 h, l;
-    split_df(d.s00, h.x, h.w);
-    split_df(d.s01, h.y, l.x);
-    split_df(d.s11, h.z, l.y);
-    l.z = l.w = 0.f;
-    // layout: h00 h01 h11 l00 | l01 l11 _ _
-    float4 *f = reinterpret_cast<float4 *>(sdiag) + 2 * (size_t)x;
-    f[0] = h;
-    f[1] = l;
-}
-
-// Number of stride classes the children c3 in [2, c4) of one U are split into.
-__host__ __device__ __forceinline__ int n_classes(int c4, uint64_t target) {
-    const uint64_t leaves = binom(c4, 3);
-    uint64_t n = (leaves + target - 1) / target;
-    if (n < 1) n = 1;
-    if (n > (uint64_t)(c4 - 2)) n = (uint64_t)(c4 - 2);
-    return (int)n;
-}
-
-template <int D>
-__host__ __device__ __forceinline__ int c4_max(int M) {
-    return D == 5 ? M - 2 : M - 1;
-}
-
-template <int D>
-__host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_t target) {
-    const uint32_t nU = D == 5 ? (uint32_t)(M - 1 - c4) : 1u;
-    return nU * (uint32_t)n_classes(c4, target);
+    if (r < binom(a.M, 3)) order3_entry<MODE>(a, r, write_p0);
 }
 
 template <int D, int MODE, int PREC>
 __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
     using SH = TreeShared<D>;
-    constexpr int NP = SH::NP;
-    constexpr int NQ = SH::NQ;
-    constexpr int PALL = NQ - 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
-    double(*const xe)[XCAP] = sh.xe();
-    float(*const xf)[XCAP] = sh.xf();
     const int tid = threadIdx.x;
     const int M = a.M;
     const int c4hi = c4_max<D>(M);
     const int K = c4hi - 2;  // c4 runs c4hi, c4hi-1, .., 3
     double *const slot = a.scratch + (size_t)blockIdx.x * a.slot_doubles;
-    double *const sdiag = slot + 4 * binom2(M);
-    const double *__restrict__ A = a.A;
 
     // prefix of item counts over c4 in descending order (warp 0, chunked scan)
     if (tid < 32) {
@@ -347,7 +101,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
         __syncthreads();
         const uint32_t item = sh.item;
         if (item >= total_items) break;
-        // ---- decode item -> (c4, c5, class s of nc)
+        // decode item -> (c4, c5, class s of nc)
         int lo = 0, hi = K;  // find k with c4pref[k] <= item < c4pref[k+1]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -359,213 +113,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
         const uint32_t rr = item - sh.c4pref[lo];
         const int u = (int)(rr / nc), s = (int)(rr % nc);
         const int c5 = (D == 5) ? c4 + 1 + u : M;
-
-        // ---- Schur complement of A after eliminating U, modes < c4 -> slot
-        // uniform pivots: m5 = chol(A[c5,c5])^{-1}, y5(c4), m4 = chol(Pi4)^{-1}
-        if (tid == 0) {
-            bool ok = true, ok2 = true;
-            double dd;
-            LInv m5{0, 0, 0};
-            Blk y5c4{0, 0, 0, 0};
-            Sym pi4 = blk_sym(ablk(A, M, c4, c4));
-            if (D == 5) {
-                m5 = chol2_inv(blk_sym(ablk(A, M, c5, c5)), ok, dd);
-                y5c4 = lmul(m5, ablk(A, M, c5, c4));
-                pi4 = sym_sub_gram(pi4, y5c4);
-            }
-            const LInv m4 = chol2_inv(pi4, ok2, dd);
-            if (!ok || !ok2) flag_status(a.status, ST_NOT_POSDEF);
-            sh.upiv[0] = m5.m00; sh.upiv[1] = m5.m10; sh.upiv[2] = m5.m11;
-            sh.upiv[3] = m4.m00; sh.upiv[4] = m4.m10; sh.upiv[5] = m4.m11;
-        }
-        __syncthreads();
-        {
-            // Y(x) = [y5(x); y4(x)] into the x-entry area (it is free until the batches start)
-            double *Y = &xe[0][0];  // 8 doubles per x, x < c4 <= GBS_MAX_MODES: 8*1024*8 <= XBYTES
-            const LInv m5{sh.upiv[0], sh.upiv[1], sh.upiv[2]};
-            const LInv m4{sh.upiv[3], sh.upiv[4], sh.upiv[5]};
-            Blk y5c4{0, 0, 0, 0};
-            if (D == 5) y5c4 = lmul(m5, ablk(A, M, c5, c4));
-            for (int x = tid; x < c4; x += TREE_THREADS) {
-                Blk y5{0, 0, 0, 0};
-                Blk r4 = ablk(A, M, c4, x);
-                if (D == 5) {
-                    y5 = lmul(m5, ablk(A, M, c5, x));
-                    r4 = blk_sub_cross(r4, y5c4, y5);
-                }
-                const Blk y4 = lmul(m4, r4);
-                double *q = Y + 8 * x;
-                q[0] = y5.a00; q[1] = y5.a01; q[2] = y5.a10; q[3] = y5.a11;
-                q[4] = y4.a00; q[5] = y4.a01; q[6] = y4.a10; q[7] = y4.a11;
-            }
-            __syncthreads();
-            const uint32_t npairs = (uint32_t)binom2(c4);
-            for (uint32_t qi = tid; qi < npairs + (uint32_t)c4; qi += TREE_THREADS) {
-                int x, y;
-                if (qi < npairs) pair_decode(qi, x, y);
-                else x = y = (int)(qi - npairs);
-                const double *px = Y + 8 * x, *py = Y + 8 * y;
-                Blk b = ablk(A, M, x, y);
-                const Blk y5x{px[0], px[1], px[2], px[3]}, y5y{py[0], py[1], py[2], py[3]};
-                const Blk y4x{px[4], px[5], px[6], px[7]}, y4y{py[4], py[5], py[6], py[7]};
-                if (D == 5) b = blk_sub_cross(b, y5x, y5y);
-                b = blk_sub_cross(b, y4x, y4y);
-                if (qi < npairs) slot_store_pair<PREC>(slot, qi, b);
-                else slot_store_diag<PREC>(sdiag, x, Sym{b.a00, 0.5 * (b.a01 + b.a10), b.a11});
-            }
-            __syncthreads();
-        }
-
-        // ---- children c3 = c4-1-s, c4-1-s-nc, ... >= 2, processed in batches
-        const int cfirst = c4 - 1 - s;
-        const int nchild = (cfirst >= 2) ? (cfirst - 2) / nc + 1 : 0;
-        int k0 = 0;
-        while (k0 < nchild) {
-            // batch [k0, k0+nb): identical arithmetic in every thread
-            int nb = 0, xs = 0;
-            while (k0 + nb < nchild && nb < CCAP) {
-                const int c3 = cfirst - (k0 + nb) * nc;
-                if (xs + c3 > XCAP) break;
-                xs += c3;
-                ++nb;
-            }
-            // pre-setup: one thread per child
-            if (tid < nb) {
-                const int b = tid;
-                const int c3 = cfirst - (k0 + b) * nc;
-                int xo = 0;
-                uint32_t lp = 0;
-                for (int q = 0; q < b; ++q) {
-                    const int cq = cfirst - (k0 + q) * nc;
-                    xo += cq;
-                    lp += (uint32_t)binom2(cq);
-                }
-                sh.c3[b] = c3;
-                sh.xoff[b] = xo;
-                sh.lpref[b] = lp;
-                if (b == nb - 1) {
-                    sh.xoff[nb] = xo + c3;
-                    sh.lpref[nb] = lp + (uint32_t)binom2(c3);
-                }
-                int P[3] = {c3, c4, c5};
-                uint64_t idxQ[NQ];
-                child_bases<NP>(P, M, sh.baseJ[b], sh.baseT[b], idxQ);
-                sh.p0R[b][0] = 0.0;
-#pragma unroll
-                for (int q = 1; q < NQ; ++q) sh.p0R[b][q] = a.p0[idxQ[q]];
-                bool ok;
-                double dd;
-                const Sym p3 = slot_diag_f64<PREC>(sdiag, c3);
-                const LInv m3 = chol2_inv(p3, ok, dd);
-                if (!ok) flag_status(a.status, ST_NOT_POSDEF);
-                sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
-            }
-            __syncthreads();
-            // setup: eliminate c3 for every x < c3 of every child in the batch
-            for (int e = tid; e < xs; e += TREE_THREADS) {
-                int lo2 = 0, hi2 = nb;
-                while (hi2 - lo2 > 1) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if (sh.xoff[mid] <= e) lo2 = mid;
-                    else hi2 = mid;
-                }
-                const int b = lo2;
-                const int c3 = sh.c3[b];
-                const int x = e - sh.xoff[b];
-                const LInv m3{sh.m3[b][0], sh.m3[b][1], sh.m3[b][2]};
-                const Blk z = lmul(m3, slot_pair_f64<PREC>(slot, binom2(c3) + x));
-                const Sym dx = sym_sub_gram(slot_diag_f64<PREC>(sdiag, x), z);
-                if (PREC == 0) {
-                    xe[0][e] = z.a00; xe[1][e] = z.a01; xe[2][e] = z.a10; xe[3][e] = z.a11;
-                    xe[4][e] = dx.s00; xe[5][e] = dx.s01; xe[6][e] = dx.s11;
-                    if (x >= 1) {
-                        bool ok;
-                        double dd;
-                        const LInv m2 = chol2_inv(dx, ok, dd);
-                        if (!ok) flag_status(a.status, ST_NOT_POSDEF);
-                        xe[7][e] = m2.m00; xe[8][e] = m2.m10; xe[9][e] = m2.m11;
-                    }
-                } else {
-                    split_df(z.a00, xf[0][e], xf[4][e]);
-                    split_df(z.a01, xf[1][e], xf[5][e]);
-                    split_df(z.a10, xf[2][e], xf[6][e]);
-                    split_df(z.a11, xf[3][e], xf[7][e]);
-                    split_df(dx.s00, xf[8][e], xf[11][e]);
-                    split_df(dx.s01, xf[9][e], xf[12][e]);
-                    split_df(dx.s11, xf[10][e], xf[13][e]);
-                    if (x >= 1) {
-                        // FP32 Cholesky factor of the c2 pivot d(x), its inverse, and the
-                        // exact residual d - l l^T (FP32 products are exact in FP64)
-                        const float pa = xf[8][e], pb = xf[9][e], pc = xf[10][e];
-                        const float i0 = rsqrtf(pa);
-                        const float l00 = pa * i0, l10 = pb * i0;
-                        const float pq = __fmaf_rn(-l10, l10, pc);
-                        const float i1 = rsqrtf(pq);
-                        const float l11 = pq * i1;
-                        if (!(pa > 0.f) || !(pq > 0.f)) flag_status(a.status, ST_NOT_POSDEF);
-                        xf[14][e] = l00; xf[15][e] = l10; xf[16][e] = l11;
-                        xf[17][e] = i0; xf[18][e] = -l10 * i0 * i1; xf[19][e] = i1;
-                        const double L00 = l00, L10 = l10, L11 = l11;
-                        xf[20][e] = __double2float_rn(fma(-L00, L00, dx.s00));
-                        xf[21][e] = __double2float_rn(fma(-L00, L10, dx.s01));
-                        xf[22][e] = __double2float_rn(fma(-L11, L11, fma(-L10, L10, dx.s11)));
-                    }
-                }
-            }
-            __syncthreads();
-            // leaves (c2, j), j < c2 < c3, flattened over the batch
-            const uint32_t L = sh.lpref[nb];
-            for (uint32_t g = tid; g < L; g += TREE_THREADS) {
-                int lo2 = 0, hi2 = nb;
-                while (hi2 - lo2 > 1) {
-                    const int mid = (lo2 + hi2) >> 1;
-                    if (sh.lpref[mid] <= g) lo2 = mid;
-                    else hi2 = mid;
-                }
-                const int b = lo2;
-                const uint32_t t = g - sh.lpref[b];
-                int c2, j;
-                pair_decode(t, c2, j);
-                const int xo = sh.xoff[b];
-                const int e2 = xo + c2, ej = xo + j;
-                const uint64_t *bJ = sh.baseJ[b];
-                const uint64_t *bT = sh.baseT[b];
-                const double P0Sp = a.p0[bJ[PALL] + c2];
-                double P0;
-                bool ok;
-                if (PREC == 0) {
-                    const Blk z2{xe[0][e2], xe[1][e2], xe[2][e2], xe[3][e2]};
-                    const Blk zj{xe[0][ej], xe[1][ej], xe[2][ej], xe[3][ej]};
-                    const LInv m2{xe[7][e2], xe[8][e2], xe[9][e2]};
-                    const Sym dj{xe[4][ej], xe[5][ej], xe[6][ej]};
-                    const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
-                    const Sym sch = sym_sub_gram(dj, lmul(m2, X));
-                    const double det2 = det_sym(sch);
-                    P0 = P0Sp * rsqrt(det2);
-                    ok = det2 > 0.0;
-                } else {
-                    const float4 *fs = reinterpret_cast<const float4 *>(slot) + 2 * (size_t)t;
-                    const float4 sh4 = fs[0], sl4 = fs[1];
-                    const DFBlk S{sh4.x, sh4.y, sh4.z, sh4.w, sl4.x, sl4.y, sl4.z, sl4.w};
-                    const DFBlk z2{xf[0][e2], xf[1][e2], xf[2][e2], xf[3][e2], xf[4][e2], xf[5][e2], xf[6][e2], xf[7][e2]};
-                    const DFBlk zj{xf[0][ej], xf[1][ej], xf[2][ej], xf[3][ej], xf[4][ej], xf[5][ej], xf[6][ej], xf[7][ej]};
-                    const DFSym dj{xf[8][ej], xf[9][ej], xf[10][ej], xf[11][ej], xf[12][ej], xf[13][ej]};
-                    const F32Piv pv{xf[14][e2], xf[15][e2], xf[16][e2], xf[17][e2], xf[18][e2],
-                                    xf[19][e2], xf[20][e2], xf[21][e2], xf[22][e2]};
-                    P0 = refined_leaf_p0(P0Sp, S, z2, zj, dj, pv, ok);
-                }
-                if (!ok) {
-                    flag_status(a.status, ST_NOT_POSDEF);
-                    P0 = __longlong_as_double(0x7ff8000000000000ULL);
-                }
-                const double v = combine<NP, MODE>(P0, j, c2, t, bJ, bT, sh.p0R[b], a.p0, a.out);
-                const uint64_t idx = bT[PALL] + t;
-                if (write_p0) a.p0[idx] = P0;
-                if (MODE != MODE_P0) a.out[idx] = v;
-            }
-            __syncthreads();
-            k0 += nb;
-        }
+        tree_item<D, MODE, PREC>(a, sh, slot, c4, c5, s, nc, write_p0);
     }
 }
 
