@@ -131,6 +131,22 @@ int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int prec
 int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
                   void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- schedule autotuning */
+
+/* Times gbs_cumulants for this (M, kmax, precision) under each candidate
+   schedule of the prefix-tree kernels -- items per CTA (1, 2, 4, 8), children
+   per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, or 256 x 2
+   per SM when M <= 577) -- and records the fastest in a process-wide table that
+   later forward calls of that shape use. If the environment variable
+   GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and
+   rewritten after tuning (JSON). Arguments as for gbs_cumulants; kappa_out is
+   overwritten with the table. Synchronises cuda_stream (not capturable).
+   best_ms_out (host pointer, may be NULL) receives the best time in ms. The
+   schedule never changes the arithmetic: tuned and default calls return
+   identical tables. */
+int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
+                 size_t ws_bytes, void *cuda_stream, float *best_ms_out);
+
 /* ---------------------------------------------------------------- ragged batches */
 
 /* One instance of a batch: its covariance V (2M x 2M, device) and the output

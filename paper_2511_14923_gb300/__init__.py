@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
     L.gbs_workspace_bytes.argtypes = [i32, i32, i32]; L.gbs_workspace_bytes.restype = sz
     L.gbs_last_error.argtypes = []; L.gbs_last_error.restype = ctypes.c_char_p
     L.gbs_stream_status.argtypes = [vp, vp]; L.gbs_stream_status.restype = i32
+    L.gbs_autotune.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp, ctypes.POINTER(ctypes.c_float)]
+    L.gbs_autotune.restype = i32
     L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
     L.gbs_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float)]; L.gbs_timing_read.restype = i32
     L.gbs_backward_workspace_bytes.argtypes = [i32, i32]; L.gbs_backward_workspace_bytes.restype = sz
@@ -321,6 +323,18 @@ class Batch:
     def status(self):
         st = torch.cuda.current_stream(self.ws.device)
         return int(lib().gbs_stream_status(_vp(self.ws), ctypes.c_void_p(st.cuda_stream)))
+
+
+def autotune(V, kmax, precision="fp32r", workspace=None) -> float:
+    """Tune the prefix-tree schedule for this shape (see gbs_autotune); returns the best ms."""
+    V, M = _prep(V)
+    out = torch.empty(table_size(M, kmax), dtype=torch.float64, device=V.device)
+    ws = workspace or Workspace(M, kmax, precision, device=V.device)
+    st = torch.cuda.current_stream(V.device)
+    ms = ctypes.c_float(0.0)
+    _check(lib().gbs_autotune(_vp(V), M, kmax, _vp(out), PRECISIONS[precision], ctypes.c_void_p(ws.ptr), ws.nbytes,
+                              ctypes.c_void_p(st.cuda_stream), ctypes.byref(ms)))
+    return float(ms.value)
 
 
 def timing(on: bool) -> None:

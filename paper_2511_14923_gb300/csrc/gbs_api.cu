@@ -9,6 +9,7 @@
 #include "gbs_fwd.cuh"
 #include "gbs_bwd.cuh"
 #include "gbs_batch.cuh"
+#include "gbs_tune.cuh"
 
 namespace {
 
@@ -101,6 +102,10 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
     a.slots = L.slots;
     a.sms = sms;
     a.ev = nullptr;
+    const gbs::TreeCfg cfg = gbs::tuned_cfg(sms, M, kmax, precision);
+    a.grain = cfg.grain;
+    a.ccap = cfg.ccap;
+    a.variant = cfg.variant;
     if (g_timing) {
         if (!g_ev_ready) {
             for (auto &ev : g_ev)
@@ -334,6 +339,38 @@ int gbs_covariance_backward(const double *U_re, const double *U_im, const double
     cudaError_t e = gbs::launch_covariance_bwd(U_re, U_im, r, eta, M, V, grad_V, grad_r, grad_eta,
                                                static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return ok();
+}
+
+int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
+                 size_t ws_bytes, void *cuda_stream, float *best_ms_out) {
+    gbs::WsLayout L;
+    int sms = 0;
+    int rc = check_common(V, M, kmax, kappa_out, precision, workspace, ws_bytes, L, sms);
+    if (rc != GBS_OK) return rc;
+    char *w = static_cast<char *>(workspace);
+    gbs::FwdArgs a{};
+    a.V = V;
+    a.M = M;
+    a.kmax = kmax;
+    a.mode = gbs::MODE_KAPPA;
+    a.precision = precision;
+    a.A = reinterpret_cast<double *>(w + L.A_off);
+    a.p0 = reinterpret_cast<double *>(w + L.p0_off);
+    a.out = kappa_out;
+    a.status = reinterpret_cast<unsigned *>(w + L.status_off);
+    a.counters = a.status + 8;
+    a.scratch = reinterpret_cast<double *>(w + L.scratch_off);
+    a.slot_doubles = L.slot_doubles;
+    a.slots = L.slots;
+    a.sms = sms;
+    a.ev = nullptr;
+    gbs::TreeCfg best;
+    float ms = 0.f;
+    int tried = 0;
+    rc = gbs::autotune(a, static_cast<cudaStream_t>(cuda_stream), best, ms, tried);
+    if (rc != GBS_OK) return fail(rc, "autotuning launch failed");
+    if (best_ms_out) *best_ms_out = ms;
     return ok();
 }
 

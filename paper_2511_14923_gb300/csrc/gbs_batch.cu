@@ -213,7 +213,7 @@ __device__ void tree_phase(char *ws, const PlanHdr &h, const InstDev *inst, cons
         if (i < 0) break;
         const InstDev &I = inst[i];
         const FwdArgs a = inst_args(I, status, nullptr, h.slot_doubles, PREC);
-        tree_item<D, MODE_KAPPA, PREC>(a, sh, slot, c4, c5, s, nc, D < I.kmax);
+        tree_item<D, MODE_KAPPA, PREC, TREE_THREADS, XCAP>(a, sh, slot, c4, c5, s, nc, D < I.kmax, CCAP);
     }
 }
 

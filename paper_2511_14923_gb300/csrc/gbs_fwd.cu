@@ -64,9 +64,9 @@ __global__ void order3_kernel(FwdArgs a, bool write_p0) {
     if (r < binom(a.M, 3)) order3_entry<MODE>(a, r, write_p0);
 }
 
-template <int D, int MODE, int PREC>
-__global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
-    using SH = TreeShared<D>;
+template <int D, int MODE, int PREC, int NT, int XC>
+__global__ void __launch_bounds__(NT, 512 / NT) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
+    using SH = TreeShared<D, XC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
     const int tid = threadIdx.x;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
         const uint32_t rr = item - sh.c4pref[lo];
         const int u = (int)(rr / nc), s = (int)(rr % nc);
         const int c5 = (D == 5) ? c4 + 1 + u : M;
-        tree_item<D, MODE, PREC>(a, sh, slot, c4, c5, s, nc, write_p0);
+        tree_item<D, MODE, PREC, NT, XC>(a, sh, slot, c4, c5, s, nc, write_p0, a.ccap);
     }
 }
 
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) tree_kernel(FwdArgs a, uint64
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout ws_layout(int M, int kmax, int sms) {
+WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm) {
     WsLayout w{};
     size_t off = 0;
     w.status_off = off;
@@ -132,31 +132,45 @@ WsLayout ws_layout(int M, int kmax, int sms) {
     const uint64_t np0 = kmax > 1 ? order_offset(M, kmax) : 0;  // orders 1..kmax-1
     off = align256(off + sizeof(double) * (size_t)np0);
     w.scratch_off = off;
-    w.slots = sms > 0 ? sms : 1;
+    w.slots = (slots_per_sm > 0 ? slots_per_sm : 1) * (sms > 0 ? sms : 1);
     w.slot_doubles = 4 * ((size_t)binom2(M) + (size_t)M);
     if (kmax >= 4) off = align256(off + sizeof(double) * w.slot_doubles * w.slots);
     w.total = off;
     return w;
 }
 
-template <int D, int MODE, int PREC>
-static cudaError_t launch_tree(const FwdArgs &a, bool write_p0, cudaStream_t st) {
+template <int D, int MODE, int PREC, int NT, int XC>
+static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
     const int M = a.M;
     const uint64_t leaves = binom(M, D);
     if (leaves == 0) return cudaSuccess;
-    const int grid_max = a.slots < a.sms ? a.slots : a.sms;
-    uint64_t target = leaves / (2 * (uint64_t)grid_max);
+    const size_t smem = sizeof(TreeShared<D, XC>);
+    auto fn = tree_kernel<D, MODE, PREC, NT, XC>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid_max = a.sms * per_sm;
+    if (grid_max > a.slots) grid_max = a.slots;
+    const int grain = a.grain > 0 ? a.grain : kDefaultCfg.grain;
+    uint64_t target = leaves / ((uint64_t)grain * (uint64_t)grid_max);
     if (target < 256) target = 256;
     uint64_t items = 0;
     for (int c4 = c4_max<D>(M); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, target);
     if (items == 0) return cudaSuccess;
     const int grid = (int)(items < (uint64_t)grid_max ? items : (uint64_t)grid_max);
-    const size_t smem = sizeof(TreeShared<D>);
-    cudaError_t e =
-        cudaFuncSetAttribute(tree_kernel<D, MODE, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tree_kernel<D, MODE, PREC><<<grid, TREE_THREADS, smem, st>>>(a, target, write_p0);
+    fn<<<grid, NT, smem, st>>>(a, target, write_p0);
     return cudaGetLastError();
+}
+
+template <int D, int MODE, int PREC>
+static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t st) {
+    FwdArgs a = a_in;  // unset (zero) schedule fields take the defaults
+    if (a.grain <= 0) a.grain = kDefaultCfg.grain;
+    if (a.ccap <= 0 || a.ccap > CCAP) a.ccap = kDefaultCfg.ccap;
+    if (a.variant == 1 && a.M <= kVariant1MaxM) return launch_tree_v<D, MODE, PREC, 256, 576>(a, write_p0, st);
+    return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP>(a, write_p0, st);
 }
 
 template <int MODE>

@@ -23,7 +23,18 @@ struct FwdArgs {
     int slots;            // number of slots = max persistent CTAs
     int sms;              // multiprocessors on the device
     cudaEvent_t *ev;      // GBS_MAX_ORDER + 2 timing events, or nullptr
+    // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
+    // memory batch, CTA shape (0: 512 threads x 1 per SM, 1: 256 threads x 2 per SM)
+    int grain, ccap, variant;
 };
+
+// Schedule of the prefix-tree kernels for one problem shape.
+struct TreeCfg {
+    int grain, ccap, variant;
+};
+constexpr TreeCfg kDefaultCfg{2, 64, 0};
+// Largest M the 256-thread variant accepts (its shared x-entry area holds 576 modes).
+constexpr int kVariant1MaxM = 577;
 
 // Workspace layout, shared by the size query and the launcher.
 struct WsLayout {
@@ -31,7 +42,9 @@ struct WsLayout {
     size_t slot_doubles;
     int slots;
 };
-WsLayout ws_layout(int M, int kmax, int sms);
+// Reserves slots_per_sm scratch slots per multiprocessor (two cover either CTA
+// shape; with one, only the 512-thread shape runs, one CTA per multiprocessor).
+WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 2);
 
 // Queues every kernel of one forward call on stream; returns a cudaError_t.
 cudaError_t launch_forward(const FwdArgs &a, cudaStream_t stream);

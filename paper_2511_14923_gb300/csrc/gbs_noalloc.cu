@@ -78,7 +78,9 @@ extern "C" int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *k
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
         return gbs::record_error(GBS_ERR_CUDA, "no CUDA device is current");
-    const gbs::WsLayout L = gbs::ws_layout(M, kmax, sms);
+    // one scratch slot per multiprocessor: the default 512-thread schedule runs
+    // at most one CTA per multiprocessor
+    const gbs::WsLayout L = gbs::ws_layout(M, kmax, sms, 1);
     if (L.total > kNoallocScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,
@@ -111,6 +113,7 @@ extern "C" int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *k
     a.slots = L.slots;
     a.sms = sms;
     a.ev = nullptr;
+    a.variant = 0;
     e = gbs::launch_forward(a, st);
     if (e != cudaSuccess) {
         char msg[256];

@@ -168,7 +168,7 @@ __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool 
 
 // ---------------------------------------------------------------- tree kernel
 
-template <int D>
+template <int D, int XC = XCAP>
 struct TreeShared {
     static constexpr int NP = D - 2;       // |P|
     static constexpr int NQ = 1 << NP;     // subsets of P
@@ -192,10 +192,10 @@ struct TreeShared {
     // l (14-16), its inverse m (17-19), residual d - l l^T (20-22).
     // Before the batches of an item start, the same storage holds Y(x) of the
     // elimination of U (8 doubles per mode x < c4).
-    static constexpr int XBYTES = (23 * 4 > 10 * 8 ? 23 * 4 : 10 * 8) * XCAP;
+    static constexpr int XBYTES = (23 * 4 > 10 * 8 ? 23 * 4 : 10 * 8) * XC;
     alignas(16) unsigned char xraw[XBYTES];
-    __device__ double (*xe())[XCAP] { return reinterpret_cast<double(*)[XCAP]>(xraw); }
-    __device__ float (*xf())[XCAP] { return reinterpret_cast<float(*)[XCAP]>(xraw); }
+    __device__ double (*xe())[XC] { return reinterpret_cast<double(*)[XC]>(xraw); }
+    __device__ float (*xf())[XC] { return reinterpret_cast<float(*)[XC]>(xraw); }
 };
 
 // Schur-complement slot access. FP64 path: 2x2 blocks as 4 doubles. Refined
@@ -268,15 +268,16 @@ __host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_
 // One work item of the prefix-tree kernel: U = {c4, c5} (D = 5) or {c4} (D = 4),
 // children c3 = c4-1-s, c4-1-s-nc, ... >= 2 (stride class s of nc). Called by all
 // threads of the block; sh is the block's shared memory, slot its scratch slot.
-template <int D, int MODE, int PREC>
-__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, double *const slot, const int c4,
-                                          const int c5, const int s, const int nc, const bool write_p0) {
-    using SH = TreeShared<D>;
+template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP>
+__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &sh, double *const slot, const int c4,
+                                          const int c5, const int s, const int nc, const bool write_p0,
+                                          const int ccap = CCAP) {
+    using SH = TreeShared<D, XC>;
     constexpr int NP = SH::NP;
     constexpr int NQ = SH::NQ;
     constexpr int PALL = NQ - 1;
-    double(*const xe)[XCAP] = sh.xe();
-    float(*const xf)[XCAP] = sh.xf();
+    double(*const xe)[XC] = sh.xe();
+    float(*const xf)[XC] = sh.xf();
     const int tid = threadIdx.x;
     const int M = a.M;
     double *const sdiag = slot + 4 * binom2(M);
@@ -308,7 +309,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, d
         const LInv m4{sh.upiv[3], sh.upiv[4], sh.upiv[5]};
         Blk y5c4{0, 0, 0, 0};
         if (D == 5) y5c4 = lmul(m5, ablk(A, M, c5, c4));
-        for (int x = tid; x < c4; x += TREE_THREADS) {
+        for (int x = tid; x < c4; x += NT) {
             Blk y5{0, 0, 0, 0};
             Blk r4 = ablk(A, M, c4, x);
             if (D == 5) {
@@ -322,7 +323,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, d
         }
         __syncthreads();
         const uint32_t npairs = (uint32_t)binom2(c4);
-        for (uint32_t qi = tid; qi < npairs + (uint32_t)c4; qi += TREE_THREADS) {
+        for (uint32_t qi = tid; qi < npairs + (uint32_t)c4; qi += NT) {
             int x, y;
             if (qi < npairs) pair_decode(qi, x, y);
             else x = y = (int)(qi - npairs);
@@ -345,11 +346,15 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, d
     while (k0 < nchild) {
         // batch [k0, k0+nb): identical arithmetic in every thread
         int nb = 0, xs = 0;
-        while (k0 + nb < nchild && nb < CCAP) {
+        while (k0 + nb < nchild && nb < ccap) {
             const int c3 = cfirst - (k0 + nb) * nc;
-            if (xs + c3 > XCAP) break;
+            if (xs + c3 > XC) break;
             xs += c3;
             ++nb;
+        }
+        if (nb == 0) {  // a child wider than the x-entry area: reject instead of spinning
+            if (tid == 0) flag_status(a.status, ST_BAD_INDEX);
+            break;
         }
         // pre-setup: one thread per child
         if (tid < nb) {
@@ -384,7 +389,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, d
         }
         __syncthreads();
         // setup: eliminate c3 for every x < c3 of every child in the batch
-        for (int e = tid; e < xs; e += TREE_THREADS) {
+        for (int e = tid; e < xs; e += NT) {
             int lo2 = 0, hi2 = nb;
             while (hi2 - lo2 > 1) {
                 const int mid = (lo2 + hi2) >> 1;
@@ -437,7 +442,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D> &sh, d
         __syncthreads();
         // leaves (c2, j), j < c2 < c3, flattened over the batch
         const uint32_t L = sh.lpref[nb];
-        for (uint32_t g = tid; g < L; g += TREE_THREADS) {
+        for (uint32_t g = tid; g < L; g += NT) {
             int lo2 = 0, hi2 = nb;
             while (hi2 - lo2 > 1) {
                 const int mid = (lo2 + hi2) >> 1;

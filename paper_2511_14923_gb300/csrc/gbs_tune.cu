@@ -1,0 +1,170 @@
+// Autotuner for the prefix-tree schedule.
+//
+// For one problem shape (device, M, kmax, precision) it times the cumulant
+// forward pass under every candidate schedule and keeps the fastest:
+//   grain   items per CTA slot (subtree granularity: 1, 2, 4, 8),
+//   ccap    children per shared-memory batch (16 or 64),
+//   variant CTA shape (512 threads x 1 per SM, or 256 threads x 2 per SM for M <= 577).
+// Results live in a process-wide table consulted by every forward call; if the
+// environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
+// it on first use and rewritten after each tuning run (a JSON array of objects).
+// The schedule changes only the order in which entries are computed, never their
+// arithmetic, so tuned and untuned calls return identical tables.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gbs.h"
+#include "gbs_common.cuh"
+#include "gbs_fwd.cuh"
+#include "gbs_tune.cuh"
+
+namespace gbs {
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int>;  // cc, sms, M, kmax, precision
+struct Entry {
+    TreeCfg cfg;
+    float ms;
+};
+
+std::mutex g_mu;
+std::map<Key, Entry> g_table;
+bool g_loaded = false;
+
+int read_int(const char *obj, const char *end, const char *key, int &out) {
+    char pat[32];
+    snprintf(pat, sizeof pat, "\"%s\"", key);
+    const char *p = strstr(obj, pat);
+    if (!p || p > end) return 0;
+    p = strchr(p + strlen(pat), ':');
+    if (!p || p > end) return 0;
+    out = (int)strtol(p + 1, nullptr, 10);
+    return 1;
+}
+
+void load_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = getenv("GBS_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "rb");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, got);
+    fclose(f);
+    const char *p = txt.c_str();
+    while ((p = strchr(p, '{')) != nullptr) {
+        const char *end = strchr(p, '}');
+        if (!end) break;
+        int cc, sms, M, kmax, prec, grain, ccap, variant;
+        if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "M", M) &&
+            read_int(p, end, "kmax", kmax) && read_int(p, end, "precision", prec) &&
+            read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
+            read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
+            (variant == 0 || variant == 1)) {
+            g_table[Key{cc, sms, M, kmax, prec}] = Entry{TreeCfg{grain, ccap, variant}, -1.f};
+        }
+        p = end + 1;
+    }
+}
+
+void save_locked() {
+    const char *path = getenv("GBS_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    fprintf(f, "[\n");
+    size_t i = 0;
+    for (const auto &kv : g_table) {
+        const Key &k = kv.first;
+        const Entry &e = kv.second;
+        fprintf(f,
+                "  {\"cc\": %d, \"sms\": %d, \"M\": %d, \"kmax\": %d, \"precision\": %d, \"grain\": %d, "
+                "\"ccap\": %d, \"variant\": %d, \"ms\": %.4f}%s\n",
+                std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), e.cfg.grain,
+                e.cfg.ccap, e.cfg.variant, e.ms, ++i < g_table.size() ? "," : "");
+    }
+    fprintf(f, "]\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+int device_cc() {
+    int dev = 0, mj = 0, mn = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, dev);
+    return 10 * mj + mn;
+}
+
+}  // namespace
+
+TreeCfg tuned_cfg(int sms, int M, int kmax, int precision) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_locked();
+    auto it = g_table.find(Key{device_cc(), sms, M, kmax, precision});
+    return it == g_table.end() ? kDefaultCfg : it->second.cfg;
+}
+
+int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tried) {
+    std::vector<TreeCfg> cand;
+    for (int variant = 0; variant <= 1; ++variant) {
+        if (variant == 1 && a.M > kVariant1MaxM) continue;
+        for (int grain : {1, 2, 4, 8})
+            for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, ccap, variant});
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GBS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GBS_ERR_CUDA;
+    }
+    best_ms = 1e30f;
+    best = kDefaultCfg;
+    tried = 0;
+    int rc = GBS_OK;
+    for (size_t c = 0; c < cand.size() && rc == GBS_OK; ++c) {
+        a.grain = cand[c].grain;
+        a.ccap = cand[c].ccap;
+        a.variant = cand[c].variant;
+        // one untimed run per candidate, then one timed run
+        for (int rep = 0; rep < 2 && rc == GBS_OK; ++rep) {
+            if (cudaMemsetAsync(a.status, 0, 64, st) != cudaSuccess) rc = GBS_ERR_CUDA;
+            if (rep == 1) cudaEventRecord(e0, st);
+            if (rc == GBS_OK && launch_forward(a, st) != cudaSuccess) rc = GBS_ERR_CUDA;
+            if (rep == 1) cudaEventRecord(e1, st);
+        }
+        if (rc != GBS_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = GBS_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ++tried;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GBS_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_locked();
+    g_table[Key{device_cc(), a.sms, a.M, a.kmax, a.precision}] = Entry{best, best_ms};
+    save_locked();
+    return GBS_OK;
+}
+
+}  // namespace gbs
