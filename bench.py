@@ -57,8 +57,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
-    p.add_argument("--workload", choices=["m144k5", "m100k5"], default="m144k5",
-                   help="m100k5: smaller case of the same kernels for profiling (not a bench line)")
+    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100"], default="m144k5",
+                   help="m100k5: smaller case of the same kernels for profiling; batch256: the 256-instance "
+                        "ragged batch; fit100: forward + adjoint of the M=100 kmax=4 fitting loss")
     return p.parse_args()
 
 
@@ -218,10 +219,107 @@ def roofline(prec, M, order_ms, sms, sm_max_mhz):
             "flops_per_entry": FP64_FLOPS_PER_LEAF[prec], "kernel_ms": t5, "order_ms": order_ms.tolist()}
 
 
+def bench_batch(args):
+    """256 ragged instances: one batched launch (CUDA-graph replay) in the headline
+    precision vs one gbs_cumulants call per instance in FP64."""
+    import torch
+    import synthetic
+    import paper_2511_14923_gb300 as gbs
+    gbs.build()
+    insts = synthetic.batch_instances(256)
+    N = sum(gbs.table_size(x.M, x.kmax) for x in insts)
+    Vs = [torch.from_numpy(x.V).cuda() for x in insts]
+    b = gbs.Batch(Vs, [x.kmax for x in insts], args.precision)
+    b.capture()
+    for _ in range(max(args.warmup - 1, 0)):
+        b.replay()
+    if b.status() != 0:
+        raise SystemExit("batched launch reported a device error")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        b.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / args.steps
+    # per-instance FP64 launches into the same outputs
+    wss = {}
+    for x in insts:
+        key = (x.M, x.kmax)
+        if key not in wss:
+            wss[key] = gbs.Workspace(x.M, x.kmax, "fp64")
+    def per_instance(prec):
+        for V, x, o in zip(Vs, insts, b.outputs):
+            gbs.cumulants(V, x.kmax, prec, out=o, workspace=wss[(x.M, x.kmax)], check=False)
+    per_instance("fp64")
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(max(1, args.steps // 2)):
+        per_instance("fp64")
+    e1.record()
+    torch.cuda.synchronize()
+    ms_single = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    line = {"metric": "subsets/s of the 256-instance ragged batch (click-cumulant tables)", "value": N / (ms_batch * 1e-3),
+            "unit": "subsets/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": "256 instances, M~U{16..144}, kmax~U{2..5}, r~U[0.5,1.5] on the first M/2 modes, "
+                                   "eta_i~U[0.2,0.6], seed 20251118", "subsets": N, "table_bytes": N * 8,
+                       "launch": "one persistent cooperative kernel, CUDA-graph replay", "precision": args.precision},
+            "per_instance_fp64": {"ms_per_step": ms_single, "value": N / (ms_single * 1e-3), "launches": 6 * len(insts)}}
+    print(json.dumps(line), flush=True)
+
+
+def bench_fit(args):
+    """Fitting step on the M=100, kmax=4 workload: r, eta -> V -> kt -> weighted
+    squared error against a target table, then the adjoint back to r and eta."""
+    import torch
+    import synthetic
+    import paper_2511_14923_gb300 as gbs
+    gbs.build()
+    inst = synthetic.config(3)
+    tgt = synthetic.fit_target(inst)
+    M, K = inst.M, inst.kmax
+    U = torch.from_numpy(inst.U).cuda()
+    kt_t = gbs.cumulants(torch.from_numpy(tgt.V).cuda(), K)
+    w = gbs.fit_weights(M, K, device="cuda")
+    r = torch.from_numpy(inst.r).cuda().requires_grad_(True)
+    eta = torch.from_numpy(inst.eta).cuda().requires_grad_(True)
+
+    def step():
+        V = gbs.CovarianceFn.apply(r, eta, U)
+        kt = gbs.CumulantFn.apply(V, K)
+        L = (w * (kt - kt_t) ** 2).sum()
+        return torch.autograd.grad(L, (r, eta))
+
+    for _ in range(args.warmup):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    N = gbs.table_size(M, K)
+    print(json.dumps({"metric": "fitting step (forward + adjoint), M=100 kmax=4", "value": N / (ms * 1e-3),
+                      "unit": "subsets/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "M=100 kmax=4, 50 squeezers, per-mode eta; target from seed + 1",
+                                 "subsets": N, "params": 2 * M}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch256":
+        bench_batch(args)
+        return
+    if args.workload == "fit100":
+        bench_fit(args)
         return
     import torch
     import synthetic
