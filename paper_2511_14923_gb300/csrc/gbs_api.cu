@@ -93,6 +93,7 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
     a.mode = mode;
     a.precision = precision;
     a.A = reinterpret_cast<double *>(w + L.A_off);
+    a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.p0 = (mode == gbs::MODE_P0) ? out : reinterpret_cast<double *>(w + L.p0_off);
     a.out = out;
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);
@@ -246,6 +247,7 @@ int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_
     a.mode = gbs::MODE_P0;
     a.precision = GBS_FP64;
     a.A = reinterpret_cast<double *>(w + L.fwd.A_off);
+    a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.status = reinterpret_cast<unsigned *>(w + L.fwd.status_off);
     a.counters = a.status + 8;
     a.scratch = reinterpret_cast<double *>(w + L.fwd.scratch_off);
@@ -356,6 +358,7 @@ int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precis
     a.mode = gbs::MODE_KAPPA;
     a.precision = precision;
     a.A = reinterpret_cast<double *>(w + L.A_off);
+    a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.p0 = reinterpret_cast<double *>(w + L.p0_off);
     a.out = kappa_out;
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);

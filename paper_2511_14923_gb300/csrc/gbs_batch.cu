@@ -112,8 +112,8 @@ int build_plan(const gbs_instance *in, int n, int precision, int grid, char *bas
         I.out = x.kappa_out;
         I.M = x.M;
         I.kmax = x.kmax;
-        I.A = reinterpret_cast<double *>(base + off);
-        off = a256(off + sizeof(double) * 4 * (size_t)x.M * x.M);
+        I.A = reinterpret_cast<double *>(base + off);  // FP64 blocks, then the float-pair copy
+        off = a256(off + 2 * sizeof(double) * 4 * (size_t)x.M * x.M);
         I.p0 = reinterpret_cast<double *>(base + off);
         off = a256(off + sizeof(double) * (x.kmax > 1 ? order_offset(x.M, x.kmax) : 0));
         for (int d = 4; d <= 5; ++d) {
@@ -163,6 +163,7 @@ __device__ __forceinline__ FwdArgs inst_args(const InstDev &I, unsigned *status,
     a.mode = MODE_KAPPA;
     a.precision = precision;
     a.A = I.A;
+    a.Af = reinterpret_cast<float *>(I.A + 4 * (size_t)I.M * I.M);
     a.p0 = I.p0;
     a.out = I.out;
     a.status = status;
@@ -238,7 +239,9 @@ __global__ void __launch_bounds__(TREE_THREADS, 1) batched_kernel(char *ws) {
     // phase 0: packing
     for (uint64_t u = gtid; u < h.total[0]; u += nthr) {
         const int i = find_inst(pref, n, u);
-        pack_entry(inst[i].V, inst[i].M, inst[i].A, (int)(u - pref[i]));
+        pack_entry(inst[i].V, inst[i].M, inst[i].A,
+                   PREC == 1 ? reinterpret_cast<float *>(inst[i].A + 4 * (size_t)inst[i].M * inst[i].M) : nullptr,
+                   (int)(u - pref[i]));
     }
     grid.sync();
     // phases 1-3: orders 1..3

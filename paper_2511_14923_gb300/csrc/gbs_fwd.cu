@@ -41,9 +41,9 @@
 
 namespace gbs {
 
-__global__ void pack_kernel(const double *__restrict__ V, int M, double *__restrict__ A) {
+__global__ void pack_kernel(const double *__restrict__ V, int M, double *__restrict__ A, float *__restrict__ Af) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < M * M) pack_entry(V, M, A, idx);
+    if (idx < M * M) pack_entry(V, M, A, Af, idx);
 }
 
 template <int MODE>
@@ -126,8 +126,8 @@ WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm) {
     size_t off = 0;
     w.status_off = off;
     off = align256(off + 256);
-    w.A_off = off;
-    off = align256(off + sizeof(double) * 4 * (size_t)M * M);
+    w.A_off = off;  // FP64 blocks, then the float-pair copy
+    off = align256(off + 2 * sizeof(double) * 4 * (size_t)M * M);
     w.p0_off = off;
     const uint64_t np0 = kmax > 1 ? order_offset(M, kmax) : 0;  // orders 1..kmax-1
     off = align256(off + sizeof(double) * (size_t)np0);
@@ -212,7 +212,8 @@ static cudaError_t launch_mode(const FwdArgs &a, cudaStream_t st) {
 cudaError_t launch_forward(const FwdArgs &a, cudaStream_t st) {
     const int M = a.M;
     if (a.ev) cudaEventRecord(a.ev[0], st);
-    pack_kernel<<<(M * M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(a.V, M, a.A);
+    pack_kernel<<<(M * M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(
+        a.V, M, a.A, a.precision == 1 ? a.Af : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.ev) cudaEventRecord(a.ev[1], st);

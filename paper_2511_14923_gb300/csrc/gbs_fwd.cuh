@@ -14,6 +14,7 @@ struct FwdArgs {
     const double *V;      // 2M x 2M covariance (row-major, xxpp)
     int M, kmax, mode, precision;
     double *A;            // packed 2x2 blocks of (V+I)/2, M*M*4 doubles (workspace)
+    float *Af;            // the same blocks as float pairs (hi x4, lo x4), refined path (workspace)
     double *p0;           // P0 table: the output for MODE_P0, a workspace table (orders < kmax) otherwise
     double *out;          // mu or kappa table (MODE_MU / MODE_KAPPA); equals p0 for MODE_P0
     unsigned *status;     // status word (workspace)

@@ -104,6 +104,7 @@ extern "C" int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *k
     a.mode = gbs::MODE_KAPPA;
     a.precision = GBS_FP64;
     a.A = reinterpret_cast<double *>(w + L.A_off);
+    a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.p0 = reinterpret_cast<double *>(w + L.p0_off);
     a.out = kappa_out;
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);

@@ -35,6 +35,51 @@ struct F32Piv {
     float l00, l10, l11, m00, m10, m11, e00, e01, e11;
 };
 
+// FP32 value as FP64, assembled from its bits on the integer pipe (GB300 runs
+// FP32<->FP64 conversions on its narrow FP64 pipe). Zero and subnormal inputs
+// give a signed zero; inputs here are finite.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    const unsigned long long r =
+        sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)(e == 0u ? sign : r));
+}
+
+// Double-float (unevaluated FP32 pair) arithmetic on the FP32 pipe, after Dekker
+// and Knuth: products split exactly by an FMA, sums by two-sum. Relative
+// accuracy about 2^-47 per operation.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF df_norm(float s, float t) {  // fast two-sum, |s| >= |t|
+    const float r = __fadd_rn(s, t);
+    return DF{r, __fsub_rn(t, __fsub_rn(r, s))};
+}
+// a * b
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.h * b.h;
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    return df_norm(p, e);
+}
+// c - a * b
+__device__ __forceinline__ DF df_sub_mul(DF c, DF a, DF b) {
+    const float p = a.h * b.h;
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    const float s = __fadd_rn(c.h, -p);
+    const float bb = __fsub_rn(s, c.h);
+    float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
+    t = __fadd_rn(t, __fsub_rn(c.l, e));
+    return df_norm(s, t);
+}
+// c + a * b
+__device__ __forceinline__ DF df_add_mul(DF c, DF a, DF b) {
+    return df_sub_mul(c, DF{-a.h, -a.l}, b);
+}
+
 __device__ __forceinline__ void split_df(double x, float &h, float &l) {
     h = __double2float_rn(x);
     l = __double2float_rn(x - (double)h);
@@ -157,8 +202,8 @@ __device__ __forceinline__ double refined_leaf_p0(double P0Sp, const DFBlk &S, c
     const float r0 = __frcp_rn(qh);
     const float eps = -__fmaf_rn(ql, r0, __fmaf_rn(qh, r0, -1.f));
     const float eta = __fmaf_rn(eps, eps, eps) + delta * __fmaf_rn(0.125f, delta, __fmaf_rn(-0.5f, eps, -0.5f));
-    const double u = P0Sp * (double)r0;
-    return fma(u, (double)eta, u);
+    const double u = P0Sp * f2d_bits(r0);
+    return fma(u, f2d_bits(eta), u);
 }
 
 }  // namespace gbs

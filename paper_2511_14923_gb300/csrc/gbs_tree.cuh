@@ -83,7 +83,10 @@ __device__ __forceinline__ double combine(double P0S, int j, int c2, uint32_t t,
 
 // ---------------------------------------------------------------- small kernels
 
-__device__ __forceinline__ void pack_entry(const double *__restrict__ V, int M, double *__restrict__ A, int idx) {
+// Writes block idx = x*M + y of A = (V+I)/2 as 4 doubles, and (if Af is not
+// null) as 4 hi floats then 4 lo floats for the refined path.
+__device__ __forceinline__ void pack_entry(const double *__restrict__ V, int M, double *__restrict__ A,
+                                           float *__restrict__ Af, int idx) {
     const int x = idx / M, y = idx - x * M;
     const size_t n2 = 2 * (size_t)M;
     double a00 = V[x * n2 + y], a01 = V[x * n2 + y + M];
@@ -92,7 +95,18 @@ __device__ __forceinline__ void pack_entry(const double *__restrict__ V, int M, 
         a00 += 1.0;
         a11 += 1.0;
     }
-    store_blk(A + 4 * (size_t)idx, Blk{0.5 * a00, 0.5 * a01, 0.5 * a10, 0.5 * a11});
+    const Blk b{0.5 * a00, 0.5 * a01, 0.5 * a10, 0.5 * a11};
+    store_blk(A + 4 * (size_t)idx, b);
+    if (Af) {
+        float4 h, l;
+        split_df(b.a00, h.x, l.x);
+        split_df(b.a01, h.y, l.y);
+        split_df(b.a10, h.z, l.z);
+        split_df(b.a11, h.w, l.w);
+        float4 *f = reinterpret_cast<float4 *>(Af) + 2 * (size_t)idx;
+        f[0] = h;
+        f[1] = l;
+    }
 }
 
 
@@ -185,6 +199,7 @@ struct TreeShared {
     uint64_t baseT[CCAP][NQ];
     double p0R[CCAP][NQ];
     double m3[CCAP][3];
+    float m3f[CCAP][6];  // refined path: m3 as float pairs (h, l) x 3
     // Per x-entry data, structure of arrays. FP64 path (10 double rows):
     // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
     // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (23 float
@@ -303,8 +318,10 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
     }
     __syncthreads();
     {
-        // Y(x) = [y5(x); y4(x)] into the x-entry area (it is free until the batches start)
-        double *Y = &xe[0][0];  // 8 doubles per x, x < c4 <= GBS_MAX_MODES: 8*1024*8 <= XBYTES
+        // Y(x) = [y5(x); y4(x)] into the x-entry area (it is free until the batches start):
+        // 8 doubles per x (FP64 path) or 8 float pairs per x (refined path); x < c4 <= 1023
+        double *Y = &xe[0][0];
+        float *Yf = &xf[0][0];
         const LInv m5{sh.upiv[0], sh.upiv[1], sh.upiv[2]};
         const LInv m4{sh.upiv[3], sh.upiv[4], sh.upiv[5]};
         Blk y5c4{0, 0, 0, 0};
@@ -317,9 +334,14 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                 r4 = blk_sub_cross(r4, y5c4, y5);
             }
             const Blk y4 = lmul(m4, r4);
-            double *q = Y + 8 * x;
-            q[0] = y5.a00; q[1] = y5.a01; q[2] = y5.a10; q[3] = y5.a11;
-            q[4] = y4.a00; q[5] = y4.a01; q[6] = y4.a10; q[7] = y4.a11;
+            const double v[8] = {y5.a00, y5.a01, y5.a10, y5.a11, y4.a00, y4.a01, y4.a10, y4.a11};
+            if (PREC == 0) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) Y[8 * x + k] = v[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) split_df(v[k], Yf[16 * x + 2 * k], Yf[16 * x + 2 * k + 1]);
+            }
         }
         __syncthreads();
         const uint32_t npairs = (uint32_t)binom2(c4);
@@ -327,14 +349,44 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
             int x, y;
             if (qi < npairs) pair_decode(qi, x, y);
             else x = y = (int)(qi - npairs);
-            const double *px = Y + 8 * x, *py = Y + 8 * y;
-            Blk b = ablk(A, M, x, y);
-            const Blk y5x{px[0], px[1], px[2], px[3]}, y5y{py[0], py[1], py[2], py[3]};
-            const Blk y4x{px[4], px[5], px[6], px[7]}, y4y{py[4], py[5], py[6], py[7]};
-            if (D == 5) b = blk_sub_cross(b, y5x, y5y);
-            b = blk_sub_cross(b, y4x, y4y);
-            if (qi < npairs) slot_store_pair<PREC>(slot, qi, b);
-            else slot_store_diag<PREC>(sdiag, x, Sym{b.a00, 0.5 * (b.a01 + b.a10), b.a11});
+            if (PREC == 0) {
+                const double *px = Y + 8 * x, *py = Y + 8 * y;
+                Blk b = ablk(A, M, x, y);
+                const Blk y5x{px[0], px[1], px[2], px[3]}, y5y{py[0], py[1], py[2], py[3]};
+                const Blk y4x{px[4], px[5], px[6], px[7]}, y4y{py[4], py[5], py[6], py[7]};
+                if (D == 5) b = blk_sub_cross(b, y5x, y5y);
+                b = blk_sub_cross(b, y4x, y4y);
+                if (qi < npairs) slot_store_pair<PREC>(slot, qi, b);
+                else slot_store_diag<PREC>(sdiag, x, Sym{b.a00, 0.5 * (b.a01 + b.a10), b.a11});
+            } else {
+                // the same elimination in float pairs: b_uv -= sum_k y(x)_ku y(y)_kv over the
+                // pivot rows k of each eliminated mode (y as a 2x2 block {00, 01, 10, 11})
+                const float *af = a.Af + 8 * ((size_t)x * M + y);
+                DF b[4] = {{af[0], af[4]}, {af[1], af[5]}, {af[2], af[6]}, {af[3], af[7]}};
+                const float *px = Yf + 16 * x, *py = Yf + 16 * y;
+#pragma unroll
+                for (int blk = (D == 5 ? 0 : 1); blk < 2; ++blk) {
+                    const float *qx = px + 8 * blk, *qy = py + 8 * blk;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int v = 0; v < 2; ++v)
+#pragma unroll
+                            for (int k = 0; k < 2; ++k)
+                                b[2 * u + v] = df_sub_mul(b[2 * u + v], DF{qx[2 * (2 * k + u)], qx[2 * (2 * k + u) + 1]},
+                                                          DF{qy[2 * (2 * k + v)], qy[2 * (2 * k + v) + 1]});
+                }
+                if (qi < npairs) {
+                    float4 *f = reinterpret_cast<float4 *>(slot) + 2 * (size_t)qi;
+                    f[0] = make_float4(b[0].h, b[1].h, b[2].h, b[3].h);
+                    f[1] = make_float4(b[0].l, b[1].l, b[2].l, b[3].l);
+                } else {
+                    // layout: h00 h01 h11 l00 | l01 l11 _ _
+                    float4 *f = reinterpret_cast<float4 *>(sdiag) + 2 * (size_t)x;
+                    f[0] = make_float4(b[0].h, b[1].h, b[3].h, b[0].l);
+                    f[1] = make_float4(b[1].l, b[3].l, 0.f, 0.f);
+                }
+            }
         }
         __syncthreads();
     }
@@ -386,6 +438,11 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
             const LInv m3 = chol2_inv(p3, ok, dd);
             if (!ok) flag_status(a.status, ST_NOT_POSDEF);
             sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
+            if (PREC == 1) {
+                split_df(m3.m00, sh.m3f[b][0], sh.m3f[b][1]);
+                split_df(m3.m10, sh.m3f[b][2], sh.m3f[b][3]);
+                split_df(m3.m11, sh.m3f[b][4], sh.m3f[b][5]);
+            }
         }
         __syncthreads();
         // setup: eliminate c3 for every x < c3 of every child in the batch
@@ -399,10 +456,10 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
             const int b = lo2;
             const int c3 = sh.c3[b];
             const int x = e - sh.xoff[b];
-            const LInv m3{sh.m3[b][0], sh.m3[b][1], sh.m3[b][2]};
-            const Blk z = lmul(m3, slot_pair_f64<PREC>(slot, binom2(c3) + x));
-            const Sym dx = sym_sub_gram(slot_diag_f64<PREC>(sdiag, x), z);
             if (PREC == 0) {
+                const LInv m3{sh.m3[b][0], sh.m3[b][1], sh.m3[b][2]};
+                const Blk z = lmul(m3, slot_pair_f64<PREC>(slot, binom2(c3) + x));
+                const Sym dx = sym_sub_gram(slot_diag_f64<PREC>(sdiag, x), z);
                 xe[0][e] = z.a00; xe[1][e] = z.a01; xe[2][e] = z.a10; xe[3][e] = z.a11;
                 xe[4][e] = dx.s00; xe[5][e] = dx.s01; xe[6][e] = dx.s11;
                 if (x >= 1) {
@@ -413,17 +470,25 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                     xe[7][e] = m2.m00; xe[8][e] = m2.m10; xe[9][e] = m2.m11;
                 }
             } else {
-                split_df(z.a00, xf[0][e], xf[4][e]);
-                split_df(z.a01, xf[1][e], xf[5][e]);
-                split_df(z.a10, xf[2][e], xf[6][e]);
-                split_df(z.a11, xf[3][e], xf[7][e]);
-                split_df(dx.s00, xf[8][e], xf[11][e]);
-                split_df(dx.s01, xf[9][e], xf[12][e]);
-                split_df(dx.s11, xf[10][e], xf[13][e]);
+                // z(x) = m3 S_U[c3, x] and d(x) = S_U[x, x] - z^T z in float pairs (FP32 pipe)
+                const float *fs = reinterpret_cast<const float *>(slot) + 8 * (binom2(c3) + x);
+                const float *fd = reinterpret_cast<const float *>(sdiag) + 8 * x;
+                const DF S00{fs[0], fs[4]}, S01{fs[1], fs[5]}, S10{fs[2], fs[6]}, S11{fs[3], fs[7]};
+                const DF m00{sh.m3f[b][0], sh.m3f[b][1]}, m10{sh.m3f[b][2], sh.m3f[b][3]}, m11{sh.m3f[b][4], sh.m3f[b][5]};
+                const DF z00 = df_mul(m00, S00), z01 = df_mul(m00, S01);
+                const DF z10 = df_add_mul(df_mul(m10, S00), m11, S10);
+                const DF z11 = df_add_mul(df_mul(m10, S01), m11, S11);
+                const DF d00 = df_sub_mul(df_sub_mul(DF{fd[0], fd[3]}, z00, z00), z10, z10);
+                const DF d01 = df_sub_mul(df_sub_mul(DF{fd[1], fd[4]}, z00, z01), z10, z11);
+                const DF d11 = df_sub_mul(df_sub_mul(DF{fd[2], fd[5]}, z01, z01), z11, z11);
+                xf[0][e] = z00.h; xf[1][e] = z01.h; xf[2][e] = z10.h; xf[3][e] = z11.h;
+                xf[4][e] = z00.l; xf[5][e] = z01.l; xf[6][e] = z10.l; xf[7][e] = z11.l;
+                xf[8][e] = d00.h; xf[9][e] = d01.h; xf[10][e] = d11.h;
+                xf[11][e] = d00.l; xf[12][e] = d01.l; xf[13][e] = d11.l;
                 if (x >= 1) {
-                    // FP32 Cholesky factor of the c2 pivot d(x), its inverse, and the
-                    // exact residual d - l l^T (FP32 products are exact in FP64)
-                    const float pa = xf[8][e], pb = xf[9][e], pc = xf[10][e];
+                    // FP32 Cholesky factor of the c2 pivot d(x), its inverse, and the residual
+                    // d - l l^T formed exactly (two-product, two-sum)
+                    const float pa = d00.h, pb = d01.h, pc = d11.h;
                     const float i0 = rsqrtf(pa);
                     const float l00 = pa * i0, l10 = pb * i0;
                     const float pq = __fmaf_rn(-l10, l10, pc);
@@ -432,10 +497,12 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                     if (!(pa > 0.f) || !(pq > 0.f)) flag_status(a.status, ST_NOT_POSDEF);
                     xf[14][e] = l00; xf[15][e] = l10; xf[16][e] = l11;
                     xf[17][e] = i0; xf[18][e] = -l10 * i0 * i1; xf[19][e] = i1;
-                    const double L00 = l00, L10 = l10, L11 = l11;
-                    xf[20][e] = __double2float_rn(fma(-L00, L00, dx.s00));
-                    xf[21][e] = __double2float_rn(fma(-L00, L10, dx.s01));
-                    xf[22][e] = __double2float_rn(fma(-L11, L11, fma(-L10, L10, dx.s11)));
+                    EftAcc r00{d00.h, d00.l}, r01{d01.h, d01.l}, r11{d11.h, d11.l};
+                    eft_sub_prod(r00, l00, l00);
+                    eft_sub_prod(r01, l00, l10);
+                    eft_sub_prod(r11, l10, l10);
+                    eft_sub_prod(r11, l11, l11);
+                    xf[20][e] = eft_val(r00); xf[21][e] = eft_val(r01); xf[22][e] = eft_val(r11);
                 }
             }
         }
