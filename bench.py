@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--precision", choices=["fp64", "fp32r"], default="fp32r",
                    help="precision of the headline number; the other one is measured too unless --only")
     p.add_argument("--only", action="store_true", help="measure the headline precision only")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="skip gbs_autotune (untimed) before measuring; use the default schedule")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
@@ -347,6 +349,10 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    tuned = {}
+    if not args.no_autotune:
+        for p in precs:  # untimed: pick the prefix-tree schedule for this shape (cached in-process)
+            tuned[p] = gbs.autotune(V, kmax, p, workspace=wss[p])
     res = {}
     if dist:
         dist.barrier()
@@ -404,6 +410,7 @@ def main():
                            "l2": "256 MiB buffer written between steps (outside the step events); "
                                  "the 3.99 GB output also exceeds L2",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
+                "autotune_best_ms": tuned or None,
                 "wall_s_timed": res[head][2], "roofline": roofline(head, M, res[head][1], sms, sm_max),
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 6 * args.steps, "clocks": clocks}
         for p in precs[1:]:

@@ -135,8 +135,9 @@ int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int preci
 
 /* Times gbs_cumulants for this (M, kmax, precision) under each candidate
    schedule of the prefix-tree kernels -- items per CTA (1, 2, 4, 8), children
-   per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, or 256 x 2
-   per SM when M <= 577) -- and records the fastest in a process-wide table that
+   per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, 256 x 2
+   per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, and 256 x 3 when
+   M <= 577) -- and records the fastest in a process-wide table that
    later forward calls of that shape use. If the environment variable
    GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and
    rewritten after tuning (JSON). Arguments as for gbs_cumulants; kappa_out is

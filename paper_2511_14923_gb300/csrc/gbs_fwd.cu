@@ -64,8 +64,8 @@ __global__ void order3_kernel(FwdArgs a, bool write_p0) {
     if (r < binom(a.M, 3)) order3_entry<MODE>(a, r, write_p0);
 }
 
-template <int D, int MODE, int PREC, int NT, int XC>
-__global__ void __launch_bounds__(NT, 512 / NT) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
+template <int D, int MODE, int PREC, int NT, int XC, int MINB>
+__global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
     using SH = TreeShared<D, XC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
@@ -139,13 +139,13 @@ WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm) {
     return w;
 }
 
-template <int D, int MODE, int PREC, int NT, int XC>
+template <int D, int MODE, int PREC, int NT, int XC, int MINB>
 static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
     const int M = a.M;
     const uint64_t leaves = binom(M, D);
     if (leaves == 0) return cudaSuccess;
     const size_t smem = sizeof(TreeShared<D, XC>);
-    auto fn = tree_kernel<D, MODE, PREC, NT, XC>;
+    auto fn = tree_kernel<D, MODE, PREC, NT, XC, MINB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -169,8 +169,13 @@ static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t 
     FwdArgs a = a_in;  // unset (zero) schedule fields take the defaults
     if (a.grain <= 0) a.grain = kDefaultCfg.grain;
     if (a.ccap <= 0 || a.ccap > CCAP) a.ccap = kDefaultCfg.ccap;
-    if (a.variant == 1 && a.M <= kVariant1MaxM) return launch_tree_v<D, MODE, PREC, 256, 576>(a, write_p0, st);
-    return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP>(a, write_p0, st);
+    if (a.variant == 1 && a.M <= kVariant1MaxM) return launch_tree_v<D, MODE, PREC, 256, 576, 2>(a, write_p0, st);
+    if constexpr (PREC == 1) {
+        // register-lean refined kernels: 20 warps in one CTA, or 3 CTAs of 8 warps
+        if (a.variant == 2) return launch_tree_v<D, MODE, PREC, 640, XCAP, 1>(a, write_p0, st);
+        if (a.variant == 3 && a.M <= kVariant1MaxM) return launch_tree_v<D, MODE, PREC, 256, 576, 3>(a, write_p0, st);
+    }
+    return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP, 1>(a, write_p0, st);
 }
 
 template <int MODE>

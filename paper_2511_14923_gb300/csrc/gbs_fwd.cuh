@@ -25,7 +25,8 @@ struct FwdArgs {
     int sms;              // multiprocessors on the device
     cudaEvent_t *ev;      // GBS_MAX_ORDER + 2 timing events, or nullptr
     // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
-    // memory batch, CTA shape (0: 512 threads x 1 per SM, 1: 256 threads x 2 per SM)
+    // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
+    // only: 2: 640 x 1, 3: 256 x 3)
     int grain, ccap, variant;
 };
 
@@ -43,9 +44,9 @@ struct WsLayout {
     size_t slot_doubles;
     int slots;
 };
-// Reserves slots_per_sm scratch slots per multiprocessor (two cover either CTA
+// Reserves slots_per_sm scratch slots per multiprocessor (three cover every CTA
 // shape; with one, only the 512-thread shape runs, one CTA per multiprocessor).
-WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 2);
+WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 3);
 
 // Queues every kernel of one forward call on stream; returns a cudaError_t.
 cudaError_t launch_forward(const FwdArgs &a, cudaStream_t stream);

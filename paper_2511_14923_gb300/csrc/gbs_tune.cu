@@ -4,7 +4,8 @@
 // forward pass under every candidate schedule and keeps the fastest:
 //   grain   items per CTA slot (subtree granularity: 1, 2, 4, 8),
 //   ccap    children per shared-memory batch (16 or 64),
-//   variant CTA shape (512 threads x 1 per SM, or 256 threads x 2 per SM for M <= 577).
+//   variant CTA shape: 512 threads x 1 per SM; 256 x 2 per SM (M <= 577); and for
+//           the refined path 640 x 1, or 256 x 3 (M <= 577).
 // Results live in a process-wide table consulted by every forward call; if the
 // environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
 // it on first use and rewritten after each tuning run (a JSON array of objects).
@@ -70,7 +71,7 @@ void load_locked() {
             read_int(p, end, "kmax", kmax) && read_int(p, end, "precision", prec) &&
             read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
             read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
-            (variant == 0 || variant == 1)) {
+            variant >= 0 && variant <= 3) {
             g_table[Key{cc, sms, M, kmax, prec}] = Entry{TreeCfg{grain, ccap, variant}, -1.f};
         }
         p = end + 1;
@@ -118,8 +119,8 @@ TreeCfg tuned_cfg(int sms, int M, int kmax, int precision) {
 
 int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tried) {
     std::vector<TreeCfg> cand;
-    for (int variant = 0; variant <= 1; ++variant) {
-        if (variant == 1 && a.M > kVariant1MaxM) continue;
+    for (int variant = 0; variant <= (a.precision == 1 ? 3 : 1); ++variant) {
+        if ((variant == 1 || variant == 3) && a.M > kVariant1MaxM) continue;
         for (int grain : {1, 2, 4, 8})
             for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, ccap, variant});
     }
