@@ -42,6 +42,10 @@ WORKLOAD = ("M=144 kmax=5 click-cumulant table: 72 squeezers r~U[0.8,1.6] on mod
 # recursion (30).
 FP64_FLOPS_PER_LEAF = {"fp64": 72, "fp32r": 33}
 DTYPE = {"fp64": "f64", "fp32r": "f32 determinant steps refined to f64 accuracy; f64 sums"}
+# DRAM bytes (read + write) per launch of the order-5 kernel at M=144 under the
+# tuned schedules, from the ncu launch list in profiles/launches_m144k5_tuned.md.
+# Reset to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES = {"fp32r": 6.6275e9 + 4.2786e9, "fp64": 2.9781e9 + 4.2348e9}
 FP64_FMA_PER_CLK_PER_SM = 2  # nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz
 
 
@@ -213,10 +217,13 @@ def measure(gbs, torch, V, out, ws, kmax, prec, steps, warmup, flush, stream, de
 def roofline(prec, M, order_ms, sms, sm_max_mhz):
     from math import comb
     t5 = order_ms[5]
+    traffic = TRAFFIC_BYTES.get(prec) if M == 144 else None
     peak = FP64_FMA_PER_CLK_PER_SM * 2 * sms * sm_max_mhz * 1e6
     achieved = FP64_FLOPS_PER_LEAF[prec] * comb(M, 5) / (t5 * 1e-3)
     return {"bound": "alu", "kernel": f"tree_kernel<5, kappa, {prec}> (FP64 pipe)", "achieved": achieved / 1e12,
-            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                              "profiles/launches_m144k5_tuned.md" if traffic else None,
             "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock (nominal 1.25 TFLOP/s at 2.07 GHz)",
             "flops_per_entry": FP64_FLOPS_PER_LEAF[prec], "kernel_ms": t5, "order_ms": order_ms.tolist()}
 
