@@ -62,6 +62,7 @@ def _load():
     lib.orc_entries.restype = None
     lib.orc_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D]; lib.orc_tables.restype = ctypes.c_int
     lib.orc_grad.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_grad.restype = ctypes.c_int
+    lib.orc_spin_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_spin_tables.restype = ctypes.c_int
     lib.orc_num_threads.argtypes = []; lib.orc_num_threads.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -178,6 +179,18 @@ def tables(V, kmax: int):
     if rc != 0:
         raise ValueError("orc_tables rejected its arguments")
     return a, b, c
+
+
+def spin_tables(V, kmax: int):
+    """(c, kappa): spin-correlator table (Eq. correlator_sum_cov) and spin-cumulant
+    table (Eq. cumulant_corr_main), orders 1..kmax, colex order per order."""
+    V = _V(V)
+    M = V.shape[0] // 2
+    N = table_size(M, kmax)
+    c, k = np.empty(N), np.empty(N)
+    if _load().orc_spin_tables(_dp(V), M, kmax, _dp(c), _dp(k)) != 0:
+        raise ValueError("orc_spin_tables rejected its arguments")
+    return c, k
 
 
 def grad(V, kmax: int, g_kappa) -> np.ndarray:

@@ -366,6 +366,66 @@ int orc_tables(const double *V, int M, int kmax, double *p0_out, double *mu_out,
     return 0;
 }
 
+/* ---------------------------------------------------------------- spin tables */
+
+/* Spin-correlator and spin-cumulant tables (orders 1..kmax): c(S) by Eq.
+   correlator_sum_cov over the P0 entries of the subsets of S, kappa(S) by Eq.
+   cumulant_corr_main over the c entries of the blocks of S. Either output may be
+   NULL. Returns 0, or -1 on bad args. */
+int orc_spin_tables(const double *V, int M, int kmax, double *c_out, double *k_out) {
+    if (M <= 0 || kmax <= 0 || kmax > M || kmax > ORC_MAXD) return -1;
+    uint64_t N = table_offset(M, kmax + 1);
+    double *p0 = (double *)malloc(sizeof(double) * N);
+    double *c = c_out ? c_out : (double *)malloc(sizeof(double) * N);
+    orc_tables(V, M, kmax, p0, NULL, NULL);
+    for (int d = 1; d <= kmax; ++d) {
+        int64_t cnt = (int64_t)orc_binom(M, d);
+        int *sets = (int *)malloc(sizeof(int) * (size_t)cnt * d);
+        orc_enumerate(M, d, sets);
+        uint64_t off = table_offset(M, d);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < cnt; ++i) {
+            const int *S = sets + (size_t)i * d;
+            int R[ORC_MAXD];
+            double acc = 0.0;
+            for (unsigned mask = 0; mask < (1u << d); ++mask) {
+                int t = 0;
+                for (int k = 0; k < d; ++k)
+                    if (mask >> k & 1u) R[t++] = S[k];
+                acc += pow(-2.0, t) * (t ? p0[index_of(M, R, t)] : 1.0);
+            }
+            c[off + i] = ((d & 1) ? -1.0 : 1.0) * acc;
+        }
+        free(sets);
+    }
+    if (k_out) {
+        for (int d = 1; d <= kmax; ++d) {
+            int64_t cnt = (int64_t)orc_binom(M, d);
+            int *sets = (int *)malloc(sizeof(int) * (size_t)cnt * d);
+            orc_enumerate(M, d, sets);
+            uint64_t off = table_offset(M, d);
+#pragma omp parallel for schedule(static)
+            for (int64_t i = 0; i < cnt; ++i) {
+                const int *S = sets + (size_t)i * d;
+                double cor[1u << ORC_MAXD];
+                int B[ORC_MAXD];
+                cor[0] = 1.0;
+                for (unsigned mask = 1; mask < (1u << d); ++mask) {
+                    int b = 0;
+                    for (int k = 0; k < d; ++k)
+                        if (mask >> k & 1u) B[b++] = S[k];
+                    cor[mask] = c[index_of(M, B, b)];
+                }
+                k_out[off + i] = orc_cumulant_from_moments(cor, d);
+            }
+            free(sets);
+        }
+    }
+    free(p0);
+    if (!c_out) free(c);
+    return 0;
+}
+
 /* ---------------------------------------------------------------- gradient */
 
 /* dL/dV for L with dL/dkt(S) = gk[index(S)] over the whole table (orders 1..kmax).

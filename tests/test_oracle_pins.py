@@ -392,3 +392,24 @@ def test_golden_config0_tables():
     np.testing.assert_allclose(data[:, 0], p0t, rtol=1e-13)
     np.testing.assert_allclose(data[:, 1], mut, rtol=0, atol=1e-15)
     np.testing.assert_allclose(data[:, 2], kt, rtol=0, atol=1e-15)
+
+
+def test_spin_tables_match_entries_and_identity():
+    """Spin tables (lookup route) equal the from-scratch entries, and satisfy
+    Eq. cumulant_exponential against the click tables: kappa = (-2)^d kt for
+    d >= 2 and 1 - 2 mu for d = 1."""
+    inst = synthetic.random_instance(8, 4, seed=91)
+    c, k = oracle.spin_tables(inst.V, 4)
+    _, mu, kt = oracle.tables(inst.V, 4)
+    pos = 0
+    for d in range(1, 5):
+        sets = oracle.enumerate_subsets(8, d)
+        for i, S in enumerate(sets):
+            assert c[pos + i] == pytest.approx(oracle.spin_correlator(inst.V, S), abs=1e-14)
+            assert k[pos + i] == pytest.approx(oracle.spin_cumulant(inst.V, S), abs=1e-13)
+            want = 1 - 2 * mu[pos + i] if d == 1 else (-2) ** d * kt[pos + i]
+            assert k[pos + i] == pytest.approx(want, abs=1e-12)
+        pos += len(sets)
+    # single mode: c({0}) = E[(-1)^x] = 2 P0 - 1
+    V = xxpp_from_blocks([squeezed(0.6)])
+    assert oracle.spin_tables(V, 1)[0][0] == pytest.approx(2.0 / cosh(0.6) - 1.0, abs=1e-15)
