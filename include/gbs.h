@@ -102,6 +102,19 @@ const char *gbs_last_error(void);
    the next compute call that uses the workspace. */
 int gbs_stream_status(const void *workspace, void *cuda_stream);
 
+/* Spin-correlator table: c_out[...] <- c(S) = E[prod_{k in S} (-1)^{x_k}]
+   = (-1)^{|S|} sum_{R subset S} (-2)^{|R|} P0(R)  (Eq. correlator_sum_cov, hbar = 2),
+   the correlators the paper's stage 1 computes. */
+int gbs_spin_correlators(const double *V, int M, int kmax, double *c_out, int precision,
+                         void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Spin-cumulant table: kappa_out[...] <- kappa(S), the cumulant of the spins
+   (-1)^{x_k} over the partitions of S (Eq. cumulant_corr_main): the table the
+   paper's sampler consumes. Computed through Eq. cumulant_exponential:
+   kappa(S) = (-2)^{|S|} kt(S) for |S| >= 2 and 1 - 2 mu({k}) = 2 P0({k}) - 1. */
+int gbs_spin_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
+                       void *workspace, size_t ws_bytes, void *cuda_stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Per-order kernel timing. While enabled (on != 0), every forward call records

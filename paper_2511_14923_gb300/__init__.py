@@ -19,6 +19,7 @@ import torch
 __all__ = [
     "GbsError", "lib", "build", "table_size", "order_offset", "rank", "unrank", "workspace_bytes",
     "Workspace", "vacuum_probs", "click_moments", "cumulants", "PRECISIONS", "cumulants_backward",
+    "spin_correlators", "spin_cumulants",
     "covariance", "covariance_backward", "CumulantFn", "CovarianceFn", "fit_weights", "Batch",
 ]
 
@@ -76,7 +77,8 @@ def lib() -> ctypes.CDLL:
     L.gbs_batched_workspace_bytes.restype = sz
     L.gbs_batched_plan.argtypes = [ctypes.POINTER(_Instance), i32, i32, vp, sz, vp]; L.gbs_batched_plan.restype = i32
     L.gbs_cumulants_batched.argtypes = [i32, vp, vp]; L.gbs_cumulants_batched.restype = i32
-    for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants"):
+    for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants", "gbs_spin_correlators",
+                 "gbs_spin_cumulants"):
         f = getattr(L, name)
         f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
         f.restype = i32
@@ -171,6 +173,16 @@ def click_moments(V, kmax, precision="fp64", out=None, workspace=None, check=Tru
 def cumulants(V, kmax, precision="fp64", out=None, workspace=None, check=True):
     """Joint click cumulants kt(S) for every 1 <= |S| <= kmax."""
     return _forward("gbs_cumulants", V, kmax, precision, out, workspace, check)
+
+
+def spin_correlators(V, kmax, precision="fp64", out=None, workspace=None, check=True):
+    """Spin correlators c(S) = E[prod (-1)^{x_k}] for every 1 <= |S| <= kmax."""
+    return _forward("gbs_spin_correlators", V, kmax, precision, out, workspace, check)
+
+
+def spin_cumulants(V, kmax, precision="fp64", out=None, workspace=None, check=True):
+    """Spin cumulants kappa(S) (the sampler's input table) for every 1 <= |S| <= kmax."""
+    return _forward("gbs_spin_cumulants", V, kmax, precision, out, workspace, check)
 
 
 def _vp(t: torch.Tensor):

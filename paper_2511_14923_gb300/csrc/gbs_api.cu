@@ -392,4 +392,14 @@ int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int preci
     return run_forward(gbs::MODE_KAPPA, V, M, kmax, kappa_out, precision, workspace, ws_bytes, cuda_stream);
 }
 
+int gbs_spin_correlators(const double *V, int M, int kmax, double *c_out, int precision, void *workspace,
+                         size_t ws_bytes, void *cuda_stream) {
+    return run_forward(gbs::MODE_SPINC, V, M, kmax, c_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+int gbs_spin_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
+                       size_t ws_bytes, void *cuda_stream) {
+    return run_forward(gbs::MODE_SPINK, V, M, kmax, kappa_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
 }  // extern "C"

@@ -225,6 +225,8 @@ cudaError_t launch_forward(const FwdArgs &a, cudaStream_t st) {
     switch (a.mode) {
         case MODE_P0: return launch_mode<MODE_P0>(a, st);
         case MODE_MU: return launch_mode<MODE_MU>(a, st);
+        case MODE_SPINC: return launch_mode<MODE_SPINC>(a, st);
+        case MODE_SPINK: return launch_mode<MODE_SPINK>(a, st);
         default: return launch_mode<MODE_KAPPA>(a, st);
     }
 }

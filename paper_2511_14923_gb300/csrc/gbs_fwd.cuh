@@ -6,7 +6,10 @@
 
 namespace gbs {
 
-enum Mode : int { MODE_P0 = 0, MODE_MU = 1, MODE_KAPPA = 2 };
+// Table a forward call fills: vacuum probabilities, click moments, click
+// cumulants, spin correlators c(S) (Eq. correlator_sum_cov), spin cumulants
+// kappa(S) (Eq. cumulant_corr_main).
+enum Mode : int { MODE_P0 = 0, MODE_MU = 1, MODE_KAPPA = 2, MODE_SPINC = 3, MODE_SPINK = 4 };
 
 // Everything one forward call needs on the device. Tables use the layout of
 // gbs.h (order groups, colex ranks within an order).

@@ -66,18 +66,36 @@ __device__ __forceinline__ double combine(double P0S, int j, int c2, uint32_t t,
         }
         return acc;
     }
-    // MODE_KAPPA
+    if (MODE == MODE_SPINC) {
+        // c(S) = -c(S') - 2 (-1)^d sum_{R' subset S'} (-2)^{|R'|} P0({j} + R'), d = |S|
+        // (the sum of Eq. correlator_sum_cov split by whether R contains j)
+        constexpr double lead = ((NP + 2) & 1) ? 2.0 : -2.0;  // -2 (-1)^d
+        double acc = -outtab[baseJ[PALL] + c2];                // -c(S')
+#pragma unroll
+        for (int q = 0; q <= PALL; ++q) {
+            const double w = lead * ((__popc(q) & 1) ? -1.0 : 1.0) * (double)(1 << __popc(q));  // (-2)^{|q|}
+            acc = fma(w, p0tab[baseJ[q] + j], acc);
+            const double t2 = (q == PALL) ? P0S : p0tab[baseT[q] + t];
+            acc = fma(-2.0 * w, t2, acc);                      // R' = Q + {c2}
+        }
+        return acc;
+    }
+    // MODE_KAPPA: kt(S) = (-1)^d [bracket];  MODE_SPINK: kappa(S) = (-2)^d kt(S) = 2^d [bracket],
+    // with the lower-order table holding kappa = (-2)^{|Q|} kt (exact power-of-two scalings)
     double acc = fma(-p0tab[j], p0tab[baseJ[PALL] + c2], P0S);
 #pragma unroll
     for (int q = 1; q <= PALL; ++q) {
-        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
+        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? -1.0 : 1.0)
+                                               : -1.0 / (double)(2 << __popc(q));  // -2^{-(|R|+1)}, R = Q
         acc = fma(sg * outtab[baseJ[q] + j], p0tab[baseJ[PALL ^ q] + c2], acc);
     }
 #pragma unroll
     for (int q = 0; q < PALL; ++q) {
-        const double sg = (__popc(q) & 1) ? -1.0 : 1.0;
-        acc = fma(-sg * outtab[baseT[q] + t], p0R[PALL ^ q], acc);
+        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? 1.0 : -1.0)
+                                               : -1.0 / (double)(4 << __popc(q));  // R = Q + {c2}
+        acc = fma(sg * outtab[baseT[q] + t], p0R[PALL ^ q], acc);
     }
+    if (MODE == MODE_SPINK) return acc * (double)(1 << (NP + 2));
     return ((NP + 2) & 1) ? -acc : acc;
 }
 
@@ -120,7 +138,9 @@ __device__ __forceinline__ void order1_entry(const FwdArgs &a, int j, bool write
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
     }
     if (write_p0) a.p0[j] = P0;
-    if (MODE != MODE_P0) a.out[j] = 1.0 - P0;  // mu({j}) = kt({j}) = 1 - P0({j})
+    // mu({j}) = kt({j}) = 1 - P0({j});  c({j}) = kappa({j}) = 2 P0({j}) - 1
+    if (MODE == MODE_MU || MODE == MODE_KAPPA) a.out[j] = 1.0 - P0;
+    if (MODE == MODE_SPINC || MODE == MODE_SPINK) a.out[j] = fma(2.0, P0, -1.0);
 }
 
 
@@ -144,6 +164,9 @@ __device__ __forceinline__ void order2_entry(const FwdArgs &a, uint32_t t, bool 
     if (write_p0) a.p0[idx] = P0;
     if (MODE == MODE_MU) a.out[idx] = a.out[c2] - a.p0[j] + P0;
     if (MODE == MODE_KAPPA) a.out[idx] = fma(-a.p0[j], a.p0[c2], P0);
+    // c({j,c2}) = -c({c2}) - 2 (P0({j}) - 2 P0(S));  kappa(S) = 4 (P0(S) - P0({j}) P0({c2}))
+    if (MODE == MODE_SPINC) a.out[idx] = fma(4.0, P0, fma(-2.0, a.p0[j], -a.out[c2]));
+    if (MODE == MODE_SPINK) a.out[idx] = 4.0 * fma(-a.p0[j], a.p0[c2], P0);
 }
 
 
