@@ -260,6 +260,7 @@ int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_
     b.p0 = reinterpret_cast<double *>(w + L.p0_off);
     b.h = reinterpret_cast<double *>(w + L.h_off);
     b.gp0 = reinterpret_cast<double *>(w + L.gp0_off);
+    b.inv = reinterpret_cast<double *>(w + L.inv_off);
     e = gbs::launch_backward(b, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     return ok();

@@ -13,7 +13,8 @@
 //     h(R) = -sum_{empty != T subset R} P0(T) h(R - T).
 //     gP0(B) = sum_{S >= B, |S| <= kmax} g_y(S) h(S - B).
 //   * P0(T) = det(A_T)^{-1/2}, A_T = (V_T + I)/2 (Eq. vacuum_gaussian_prob):
-//     dP0(T)/dV_T = -1/2 P0(T) (V_T + I)^{-1} = -1/4 P0(T) A_T^{-1}.
+//     dP0(T)/dV_T = -1/2 P0(T) (V_T + I)^{-1} = -1/4 P0(T) A_T^{-1}; A_T^{-1} comes
+//     from A_{T'}^{-1} (T' = T minus its smallest mode) by the block inverse.
 // grad_V is the symmetric gradient: for every symmetric perturbation dV,
 // dL = sum_ab grad_V[a][b] dV[a][b].
 #include <cstdio>
@@ -62,25 +63,8 @@ __global__ void h_kernel(int M, int r, Offsets o, const double *__restrict__ p0,
     h[o.off[r] + i] = acc;
 }
 
-// gP0 scatter, order d: every nonempty B subset S receives g_y(S) h(S - B).
-__global__ void gp0_kernel(int M, int d, Offsets o, const double *__restrict__ gk, const double *__restrict__ h,
-                           double *__restrict__ gp0) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= binom(M, d)) return;
-    const double gy = ((d & 1) ? -1.0 : 1.0) * gk[o.off[d] + i];
-    if (gy == 0.0) return;
-    int s[GBS_MAX_ORDER];
-    colex_unrank(i, d, s);
-    const unsigned full = (1u << d) - 1;
-    for (unsigned b = 1; b <= full; ++b) {
-        const unsigned rest = full ^ b;
-        const double hr = rest ? h[sub_index(s, d, rest, o.off)] : 1.0;
-        atomicAdd(gp0 + sub_index(s, d, b, o.off), gy * hr);
-    }
-}
-
-// grad_V scatter, order d: -1/4 gP0(T) P0(T) A_T^{-1} into the rows/cols of T.
-// Privatised in shared memory (lower triangle of the 2M x 2M gradient) when it fits.
+// grad_V scatter, order d (used for d = 1): -1/4 gP0(T) P0(T) A_T^{-1} into the rows/cols of T,
+// optionally privatised in shared memory (lower triangle of the 2M x 2M gradient).
 template <int D>
 __global__ void gv_kernel(int M, Offsets o, const double *__restrict__ A, const double *__restrict__ p0,
                           const double *__restrict__ gp0, double *__restrict__ gV, bool private_smem,
@@ -165,8 +149,7 @@ __global__ void gv_kernel(int M, Offsets o, const double *__restrict__ A, const 
                 if (private_smem) {
                     atomicAdd(sgv + (size_t)hi * (hi + 1) / 2 + lo, v);
                 } else {
-                    atomicAdd(gV + (size_t)hi * n2 + lo, v);
-                    if (hi != lo) atomicAdd(gV + (size_t)lo * n2 + hi, v);
+                    atomicAdd(gV + (size_t)hi * n2 + lo, v);  // lower triangle; mirrored at the end
                 }
             }
         }
@@ -182,9 +165,271 @@ __global__ void gv_kernel(int M, Offsets o, const double *__restrict__ A, const 
             while ((size_t)(hi + 1) * (hi + 2) / 2 <= q) ++hi;
             const int lo = (int)(q - (size_t)hi * (hi + 1) / 2);
             atomicAdd(gV + (size_t)hi * n2 + lo, v);
-            if (hi != lo) atomicAdd(gV + (size_t)lo * n2 + hi, v);
         }
     }
+}
+
+// gP0 by gathering: for the order-b subset B,
+//   gP0(B) = sum over R disjoint from B, |R| <= kmax - b, of g_y(B + R) h(R),
+// a group of G threads per B (G = 256 for b = 1, 32 otherwise), no atomics.
+// Term index t -> (r = |R|, colex rank of R among the r-subsets of the M - b
+// modes outside B) -> R -> B + R.
+// With chunks > 1, each B's terms are split over that many groups (group index
+// = B * chunks + chunk), and the partial sums are added atomically (gp0 zeroed).
+template <int G>
+__global__ void gp0_gather_kernel(int M, int b, int kmax, Offsets o, const double *__restrict__ gk,
+                                  const double *__restrict__ h, double *__restrict__ gp0, int chunks) {
+    const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const uint64_t unit = grp / chunks;
+    const int chunk = (int)(grp % chunks);
+    const int lane = threadIdx.x % G;
+    const uint64_t nB = binom(M, b);
+    if (unit >= nB) return;  // whole groups leave together (G divides blockDim)
+    int B[GBS_MAX_ORDER];
+    colex_unrank(unit, b, B);
+    uint64_t cum[GBS_MAX_ORDER + 2];
+    cum[0] = 0;
+    const int rmax = kmax - b;
+    for (int r = 0; r <= rmax; ++r) cum[r + 1] = cum[r] + binom(M - b, r);
+    double acc = 0.0;
+    const uint64_t nterm = cum[rmax + 1];
+    const uint64_t t0 = nterm * chunk / chunks, t1 = nterm * (chunk + 1) / chunks;
+    for (uint64_t t = t0 + lane; t < t1; t += G) {
+        int r = 0;
+        while (cum[r + 1] <= t) ++r;
+        int R[GBS_MAX_ORDER], S[GBS_MAX_ORDER];
+        if (r > 0) colex_unrank(t - cum[r], r, R);
+        // complement index -> mode: skip the elements of B (sorted)
+        for (int i = 0; i < r; ++i) {
+            int m = R[i];
+            for (int q = 0; q < b; ++q)
+                if (B[q] <= m) ++m;
+            R[i] = m;
+        }
+        // S = B + R, sorted merge
+        int ib = 0, ir = 0;
+        for (int k = 0; k < b + r; ++k) S[k] = (ir >= r || (ib < b && B[ib] < R[ir])) ? B[ib++] : R[ir++];
+        uint64_t rs = 0, rr = 0;
+        for (int k = 0; k < b + r; ++k) rs += binom(S[k], k + 1);
+        for (int k = 0; k < r; ++k) rr += binom(R[k], k + 1);
+        const double gy = (((b + r) & 1) ? -1.0 : 1.0) * gk[o.off[b + r] + rs];
+        const double hr = r ? h[o.off[r] + rr] : 1.0;
+        acc = fma(gy, hr, acc);
+    }
+    // group reduction
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (G == 32) {
+        if (lane == 0) {
+            if (chunks == 1) gp0[o.off[b] + unit] = acc;
+            else atomicAdd(gp0 + o.off[b] + unit, acc);
+        }
+    } else {
+        __shared__ double red[G / 32];
+        if ((threadIdx.x & 31) == 0) red[lane >> 5] = acc;
+        __syncthreads();
+        if (lane == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < G / 32; ++w) tot += red[w];
+            if (chunks == 1) gp0[o.off[b] + unit] = tot;
+            else atomicAdd(gp0 + o.off[b] + unit, tot);
+        }
+    }
+}
+
+// gP0 for the top order: only R = empty contributes, gP0(B) = g_y(B).
+__global__ void gp0_top_kernel(uint64_t n, double sign, const double *__restrict__ gk, double *__restrict__ gp0) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) gp0[i] = sign * gk[i];
+}
+
+// A_{T'}^{-1} for every order-DP subset T' (rows x of T', then p of T'), packed
+// lower triangle (row-major) per T'. One thread per T'.
+template <int DP>
+__global__ void ainv_kernel(int M, const double *__restrict__ A, double *__restrict__ inv, unsigned *status) {
+    constexpr int N = 2 * DP, NT = N * (N + 1) / 2;
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= binom(M, DP)) return;
+    int s[DP];
+    colex_unrank(i, DP, s);
+    double a[N][N];
+#pragma unroll
+    for (int u = 0; u < DP; ++u)
+#pragma unroll
+        for (int v = 0; v < DP; ++v) {
+            const Blk bl = ablk(A, M, s[u], s[v]);
+            a[u][v] = bl.a00;
+            a[u][v + DP] = bl.a01;
+            a[u + DP][v] = bl.a10;
+            a[u + DP][v + DP] = bl.a11;
+        }
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double dkk = a[k][k];
+#pragma unroll
+        for (int m = 0; m < k; ++m) dkk = fma(-a[k][m], a[k][m], dkk);
+        ok = ok && dkk > 0.0;
+        const double ik = rsqrt(dkk);
+        a[k][k] = ik;
+#pragma unroll
+        for (int r = k + 1; r < N; ++r) {
+            double v = a[r][k];
+#pragma unroll
+            for (int m = 0; m < k; ++m) v = fma(-a[r][m], a[k][m], v);
+            a[r][k] = v * ik;
+        }
+    }
+    if (!ok) flag_status(status, ST_NOT_POSDEF);
+    // W = L^{-1} (lower), stored transposed in the upper triangle: W[r][c] at a[c][r]
+    // for r > c; the diagonal a[k][k] = 1 / L_kk is W[k][k].
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+        for (int r = c + 1; r < N; ++r) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = c; m < r; ++m) v = fma(-a[r][m], a[c][m], v);  // L[r][m] W[m][c]
+            a[c][r] = v * a[r][r];
+        }
+    double *out = inv + (size_t)i * NT;
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = r; m < N; ++m) v = fma(a[r][m], a[c][m], v);  // (W^T W)_{rc} = sum_m W_mr W_mc
+            out[q++] = v;
+        }
+}
+
+// dL/dV for the order-D subsets T = {j} + T' (j < min T'), one warp per T'
+// (order DP = D - 1), lanes over j. With A' = A_{T'}, b = A[T', j], a = A_jj,
+// u = A'^{-1} b, S = a - b^T u (the Schur complement) and v = u S^{-1}:
+//   A_T^{-1} = [[A'^{-1} + v u^T, -v], [-v^T, S^{-1}]].
+// The T' x T' block is summed over the warp's leaves and added once; the j rows
+// go straight to dV. Each contribution is C(T) A_T^{-1}, C(T) = -1/4 gP0(T) P0(T).
+template <int DP>
+__global__ void __launch_bounds__(256, 2) gv2_kernel(int M, Offsets o, const double *__restrict__ A,
+                                                     const double *__restrict__ p0, const double *__restrict__ gp0,
+                                                     const double *__restrict__ inv, double *__restrict__ gV,
+                                                     unsigned *status) {
+    constexpr int N = 2 * DP, NT = N * (N + 1) / 2, D = DP + 1;
+    __shared__ double sai[8][NT];  // the warp's A_{T'}^{-1} (blockDim 256 = 8 warps)
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (w >= binom(M, DP)) return;  // whole warps leave together; no block barrier below
+    int s[DP];
+    colex_unrank(w, DP, s);
+    const int n2 = 2 * M;
+    const double *Ai = inv + (size_t)w * NT;
+    double *ai = sai[wib];
+    for (int q = lane; q < NT; q += 32) ai[q] = Ai[q];
+    __syncwarp();
+    auto AI = [&](int r, int c) { return r >= c ? ai[r * (r + 1) / 2 + c] : ai[c * (c + 1) / 2 + r]; };
+    int gr[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) gr[u] = u < DP ? s[u] : s[u - DP] + M;
+    // rank of T = {j} + T' is baseT + j
+    uint64_t baseT = o.off[D];
+#pragma unroll
+    for (int u = 0; u < DP; ++u) baseT += binom(s[u], u + 2);
+    double sumC = 0.0, acc[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) acc[q] = 0.0;
+    for (int j = lane; j < s[0]; j += 32) {
+        const double g = gp0[baseT + j];
+        if (g == 0.0) continue;
+        const double C = -0.25 * g * p0[baseT + j];
+        double b[N][2];
+#pragma unroll
+        for (int u = 0; u < DP; ++u) {
+            const Blk bl = ablk(A, M, s[u], j);
+            b[u][0] = bl.a00;
+            b[u][1] = bl.a01;
+            b[u + DP][0] = bl.a10;
+            b[u + DP][1] = bl.a11;
+        }
+        double uu[N][2];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            double x0 = 0.0, x1 = 0.0;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const double aic = AI(r, c);
+                x0 = fma(aic, b[c][0], x0);
+                x1 = fma(aic, b[c][1], x1);
+            }
+            uu[r][0] = x0;
+            uu[r][1] = x1;
+        }
+        const Sym ajj = blk_sym(ablk(A, M, j, j));
+        double S00 = ajj.s00, S01 = ajj.s01, S11 = ajj.s11;
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            S00 = fma(-b[r][0], uu[r][0], S00);
+            S01 = fma(-b[r][0], uu[r][1], S01);
+            S11 = fma(-b[r][1], uu[r][1], S11);
+        }
+        const double det = fma(-S01, S01, S00 * S11);
+        if (!(det > 0.0) || !(S00 > 0.0)) {
+            flag_status(status, ST_NOT_POSDEF);
+            continue;
+        }
+        const double id = 1.0 / det;
+        const double i00 = S11 * id, i01 = -S01 * id, i11 = S00 * id;  // S^{-1}
+        sumC += C;
+        double cv[N][2];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            cv[r][0] = C * fma(uu[r][0], i00, uu[r][1] * i01);
+            cv[r][1] = C * fma(uu[r][0], i01, uu[r][1] * i11);
+        }
+        int q = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c, ++q) acc[q] = fma(cv[r][0], uu[c][0], fma(cv[r][1], uu[c][1], acc[q]));
+        // j rows: -C v against T', C S^{-1} on the j block; lower triangle only
+        // (row >= column), mirrored at the end
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            const int g0 = gr[r];
+            atomicAdd(gV + (size_t)g0 * n2 + j, -cv[r][0]);  // g0 > j
+            const int jm = j + M;
+            if (g0 >= jm) atomicAdd(gV + (size_t)g0 * n2 + jm, -cv[r][1]);
+            else atomicAdd(gV + (size_t)jm * n2 + g0, -cv[r][1]);
+        }
+        atomicAdd(gV + (size_t)j * n2 + j, C * i00);
+        atomicAdd(gV + (size_t)(j + M) * n2 + j, C * i01);
+        atomicAdd(gV + (size_t)(j + M) * n2 + j + M, C * i11);
+    }
+    // warp reduction of the T' x T' block
+    for (int off = 16; off > 0; off >>= 1) {
+        sumC += __shfl_down_sync(0xffffffffu, sumC, off);
+#pragma unroll
+        for (int q = 0; q < NT; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
+    }
+    if (lane == 0 && sumC != 0.0) {
+        int q = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c, ++q) {
+                const double v = fma(sumC, ai[q], acc[q]);
+                const int hi = gr[r] > gr[c] ? gr[r] : gr[c], lo = gr[r] > gr[c] ? gr[c] : gr[r];
+                atomicAdd(gV + (size_t)hi * n2 + lo, v);
+            }
+    }
+}
+
+// Mirror the accumulated lower triangle of dV into the upper triangle.
+__global__ void mirror_kernel(int n2, double *__restrict__ gV) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n2 * n2) return;
+    const int r = (int)(idx / n2), c = (int)(idx % n2);
+    if (r < c) gV[idx] = gV[(size_t)c * n2 + r];
 }
 
 BwdLayout bwd_layout(int M, int kmax, int sms) {
@@ -198,6 +443,10 @@ BwdLayout bwd_layout(int M, int kmax, int sms) {
     off += ((sizeof(double) * order_offset(M, kmax) + 255) & ~(size_t)255);
     b.gp0_off = off;
     off += ((sizeof(double) * N + 255) & ~(size_t)255);
+    // inverses of A_{T'} for the largest prefix order kmax - 1 (reused per order)
+    const int dp = kmax - 1;
+    b.inv_off = off;
+    if (dp >= 1) off += ((sizeof(double) * binom(M, dp) * (size_t)(dp * (2 * dp + 1)) + 255) & ~(size_t)255);
     b.total = off;
     return b;
 }
@@ -218,43 +467,52 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
         h_kernel<<<(unsigned)((n + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(M, r, o, a.p0, a.h);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // 3. gP0 = sum over supersets
-    const uint64_t N = order_offset(M, K + 1);
-    if ((e = cudaMemsetAsync(a.gp0, 0, sizeof(double) * N, st)) != cudaSuccess) return e;
-    for (int d = 1; d <= K; ++d) {
-        const uint64_t n = binom(M, d);
-        gp0_kernel<<<(unsigned)((n + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(M, d, o, a.gk, a.h,
-                                                                                           a.gp0);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    // 4. grad_V
-    const size_t n2 = 2 * (size_t)M;
-    if ((e = cudaMemsetAsync(a.gV, 0, sizeof(double) * n2 * n2, st)) != cudaSuccess) return e;
-    const size_t tri_bytes = sizeof(double) * n2 * (n2 + 1) / 2;
-    const bool priv = tri_bytes <= 200 * 1024;
-    const size_t smem = priv ? tri_bytes : 0;
-    for (int d = 1; d <= K; ++d) {
-        const uint64_t n = binom(M, d);
-        uint64_t blocks = (n + BWD_THREADS - 1) / BWD_THREADS;
-        const uint64_t cap = priv ? (uint64_t)a.fwd.sms : (uint64_t)a.fwd.sms * 8;
-        if (blocks > cap) blocks = cap;
-        switch (d) {
-#define GV_CASE(DD)                                                                                           \
-    case DD:                                                                                                  \
-        if (priv && (e = cudaFuncSetAttribute(gv_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                              (int)smem)) != cudaSuccess)                                      \
-            return e;                                                                                         \
-        gv_kernel<DD><<<(unsigned)blocks, BWD_THREADS, smem, st>>>(M, o, f.A, a.p0, a.gp0, a.gV, priv, f.status); \
-        break;
-            GV_CASE(1)
-            GV_CASE(2)
-            GV_CASE(3)
-            GV_CASE(4)
-            GV_CASE(5)
-#undef GV_CASE
+    // 3. gP0 by gathering over supersets (one group per subset B)
+    for (int b = 1; b <= K; ++b) {
+        const uint64_t n = binom(M, b);
+        if (b == K) {
+            gp0_top_kernel<<<(unsigned)((n + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(
+                n, (K & 1) ? -1.0 : 1.0, a.gk + o.off[K], a.gp0 + o.off[K]);
+        } else if (b == 1) {
+            // few units with many terms each: split each B over several CTAs
+            int chunks = (int)((4 * (uint64_t)a.fwd.sms + n - 1) / n);
+            if (chunks < 1) chunks = 1;
+            if ((e = cudaMemsetAsync(a.gp0, 0, sizeof(double) * n, st)) != cudaSuccess) return e;
+            gp0_gather_kernel<256><<<(unsigned)(n * chunks), 256, 0, st>>>(M, b, K, o, a.gk, a.h, a.gp0, chunks);
+        } else {
+            const uint64_t thr = n * 32;
+            gp0_gather_kernel<32><<<(unsigned)((thr + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(
+                M, b, K, o, a.gk, a.h, a.gp0, 1);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // 4. grad_V: order 1 directly, higher orders per prefix T'
+    const size_t n2 = 2 * (size_t)M;
+    if ((e = cudaMemsetAsync(a.gV, 0, sizeof(double) * n2 * n2, st)) != cudaSuccess) return e;
+    gv_kernel<1><<<(unsigned)((M + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(M, o, f.A, a.p0, a.gp0,
+                                                                                       a.gV, false, f.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int d = 2; d <= K; ++d) {
+        const uint64_t nt = binom(M, d - 1);
+        const unsigned gi = (unsigned)((nt + BWD_THREADS - 1) / BWD_THREADS);
+        const unsigned gw = (unsigned)((nt * 32 + BWD_THREADS - 1) / BWD_THREADS);
+        switch (d) {
+#define GV2_CASE(DD)                                                                                        \
+    case DD:                                                                                                \
+        ainv_kernel<DD - 1><<<gi, BWD_THREADS, 0, st>>>(M, f.A, a.inv, f.status);                          \
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;                                             \
+        gv2_kernel<DD - 1><<<gw, BWD_THREADS, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status);      \
+        break;
+            GV2_CASE(2)
+            GV2_CASE(3)
+            GV2_CASE(4)
+            GV2_CASE(5)
+#undef GV2_CASE
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mirror_kernel<<<(unsigned)((n2 * n2 + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>((int)n2, a.gV);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

@@ -6,7 +6,7 @@ namespace gbs {
 
 struct BwdLayout {
     WsLayout fwd;                     // packing, status, lower-order P0 slots, scratch slots
-    size_t p0_off, h_off, gp0_off, total;
+    size_t p0_off, h_off, gp0_off, inv_off, total;
 };
 BwdLayout bwd_layout(int M, int kmax, int sms);
 
@@ -18,6 +18,7 @@ struct BwdArgs {
     double *p0;         // P0 table, all orders (workspace)
     double *h;          // inverse-moment table, orders < kmax (workspace)
     double *gp0;        // dL/dP0 table (workspace)
+    double *inv;        // inverses of A_{T'} for one prefix order (workspace)
 };
 
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st);

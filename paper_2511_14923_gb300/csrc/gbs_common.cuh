@@ -15,13 +15,19 @@ enum : unsigned {
 };
 
 // ---------------------------------------------------------------- combinatorics
-// C(n, k) for 0 <= k <= 6 and 0 <= n <= 4096 by closed-form products; exact in
-// 64-bit arithmetic over that range (each partial product is a binomial times a
-// small factor). Negative or short n gives 0.
+// C(n, k) for 0 <= k <= 6 and 0 <= n <= 1030 (n^6 < 2^64); 0 if n < k or k < 0.
+// Each step r <- r (n - i) / (i + 1) keeps r = C(n, i + 1) exact, and the
+// divisors are constants, so no runtime 64-bit division is emitted.
 __host__ __device__ __forceinline__ uint64_t binom(int n, int k) {
     if (n < k || k < 0) return 0;
+    const uint64_t N = (uint64_t)n;
     uint64_t r = 1;
-    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    if (k >= 1) r = N;
+    if (k >= 2) r = r * (N - 1) / 2;
+    if (k >= 3) r = r * (N - 2) / 3;
+    if (k >= 4) r = r * (N - 3) / 4;
+    if (k >= 5) r = r * (N - 4) / 5;
+    if (k >= 6) r = r * (N - 5) / 6;
     return r;
 }
 
