@@ -63,6 +63,9 @@ def _load():
     lib.orc_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D]; lib.orc_tables.restype = ctypes.c_int
     lib.orc_grad.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_grad.restype = ctypes.c_int
     lib.orc_spin_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_spin_tables.restype = ctypes.c_int
+    lib.orc_p0_displaced.argtypes = [D, D, ctypes.c_int, I, ctypes.c_int]; lib.orc_p0_displaced.restype = ctypes.c_double
+    lib.orc_entries_displaced.argtypes = [D, D, ctypes.c_int, ctypes.c_int, I, ctypes.c_int64, D, D, D]
+    lib.orc_entries_displaced.restype = None
     lib.orc_num_threads.argtypes = []; lib.orc_num_threads.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -167,6 +170,34 @@ def entries(V, sets, want=("p0", "mu", "kappa")):
                         _dp(outs["mu"]) if "mu" in outs else null,
                         _dp(outs["kappa"]) if "kappa" in outs else null)
     return outs
+
+
+def p0_displaced(V, mean, S) -> float:
+    V = _V(V); S = _S(S)
+    m = np.ascontiguousarray(mean, dtype=np.float64)
+    return _load().orc_p0_displaced(_dp(V), _dp(m), V.shape[0] // 2, _ip(S), S.size)
+
+
+def entries_displaced(V, mean, sets, want=("p0", "mu", "kappa")):
+    """Displaced-state entries (Eq. vacuum_gaussian_prob with first moments) for each
+    row of sets, each from scratch."""
+    V = _V(V); sets = _S(sets)
+    m = np.ascontiguousarray(mean, dtype=np.float64)
+    n, d = sets.shape
+    outs = {k: np.empty(n) for k in want}
+    null = ctypes.POINTER(ctypes.c_double)()
+    _load().orc_entries_displaced(_dp(V), _dp(m), V.shape[0] // 2, d, _ip(sets), n,
+                                  _dp(outs["p0"]) if "p0" in outs else null,
+                                  _dp(outs["mu"]) if "mu" in outs else null,
+                                  _dp(outs["kappa"]) if "kappa" in outs else null)
+    return outs
+
+
+def tables_displaced(V, mean, kmax: int):
+    """(P0, mu, kappa) tables of a displaced state, every entry from scratch."""
+    M = _V(V).shape[0] // 2
+    outs = [entries_displaced(V, mean, enumerate_subsets(M, d)) for d in range(1, kmax + 1)]
+    return tuple(np.concatenate([o[k] for o in outs]) for k in ("p0", "mu", "kappa"))
 
 
 def tables(V, kmax: int):

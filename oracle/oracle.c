@@ -123,6 +123,59 @@ double orc_p0(const double *V, int M, const int *T, int t) {
     return 1.0 / sqrt(det);
 }
 
+double orc_cumulant_from_moments(const double *mom, int d);
+
+/* Displaced state (first moments mean[2M], xxpp, hbar = 2): the full Eq.
+   vacuum_gaussian_prob, P0(T) = exp(-1/2 m_T^T (V_T + I)^{-1} m_T) / sqrt(det((V_T + I)/2)),
+   with (V_T + I)^{-1} m_T from Gauss-Jordan elimination. */
+double orc_p0_displaced(const double *V, const double *mean, int M, const int *T, int t) {
+    double a[ORC_MAXN * ORC_MAXN], b[ORC_MAXN * ORC_MAXN], inv[ORC_MAXN * ORC_MAXN];
+    if (t == 0) return 1.0;
+    if (t > ORC_MAXD) return NAN;
+    int n = 2 * t;
+    reduced_A(V, M, T, t, a);
+    memcpy(b, a, sizeof(double) * n * n);
+    double det = det_lu(b, n);
+    if (!(det > 0.0)) return NAN;
+    for (int q = 0; q < n * n; ++q) a[q] *= 2.0; /* V_T + I */
+    if (inv_gj(a, inv, n) != 0) return NAN;
+    double m[ORC_MAXN], quad = 0.0;
+    for (int i = 0; i < n; ++i) m[i] = mean[(i < t) ? T[i] : T[i - t] + M];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) quad += m[i] * inv[i * n + j] * m[j];
+    return exp(-0.5 * quad) / sqrt(det);
+}
+
+/* Entries of a displaced state for n sorted d-subsets, from scratch: P0 by the
+   formula above, mu by inclusion-exclusion over subsets, the click cumulant by
+   the partition sum over the moments of the blocks. Any output may be NULL. */
+void orc_entries_displaced(const double *V, const double *mean, int M, int d, const int *sets, int64_t n,
+                           double *p0, double *mu, double *kt) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        const int *S = sets + (size_t)i * d;
+        double pm[1u << ORC_MAXD], mom[1u << ORC_MAXD];
+        int T[ORC_MAXD];
+        for (unsigned mask = 0; mask < (1u << d); ++mask) {
+            int t = 0;
+            for (int k = 0; k < d; ++k)
+                if (mask >> k & 1u) T[t++] = S[k];
+            pm[mask] = orc_p0_displaced(V, mean, M, T, t);
+        }
+        for (unsigned mask = 0; mask < (1u << d); ++mask) {
+            double acc = 0.0;
+            for (unsigned sub = mask;; sub = (sub - 1) & mask) {
+                acc += ((__builtin_popcount(sub) & 1) ? -1.0 : 1.0) * pm[sub];
+                if (sub == 0) break;
+            }
+            mom[mask] = acc;
+        }
+        if (p0) p0[i] = pm[(1u << d) - 1];
+        if (mu) mu[i] = mom[(1u << d) - 1];
+        if (kt) kt[i] = orc_cumulant_from_moments(mom, d);
+    }
+}
+
 /* ---------------------------------------------------------------- click moments */
 
 /* mu(S) = sum_{T subset S} (-1)^{|T|} P0(T), each P0 from its own determinant. */

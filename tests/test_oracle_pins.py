@@ -413,3 +413,92 @@ def test_spin_tables_match_entries_and_identity():
     # single mode: c({0}) = E[(-1)^x] = 2 P0 - 1
     V = xxpp_from_blocks([squeezed(0.6)])
     assert oracle.spin_tables(V, 1)[0][0] == pytest.approx(2.0 / cosh(0.6) - 1.0, abs=1e-15)
+
+
+# ------------------------------------------------------------------ displaced states (Eq. vacuum_gaussian_prob, mu != 0)
+
+@pytest.mark.parametrize("alpha", [0.0, 0.4 + 0.3j, -1.1j, 1.7])
+def test_coherent_state_vacuum_probability(alpha):
+    """Coherent state |alpha>: V = I, first moments (2 Re alpha, 2 Im alpha) for
+    hbar = 2, vacuum probability exp(-|alpha|^2)."""
+    V = np.eye(2)
+    m = np.array([2 * alpha.real if isinstance(alpha, complex) else 2 * alpha,
+                  2 * alpha.imag if isinstance(alpha, complex) else 0.0])
+    assert oracle.p0_displaced(V, m, [0]) == pytest.approx(np.exp(-abs(alpha) ** 2), rel=1e-14)
+
+
+def test_displaced_product_state_factorises_and_zero_mean_reduces():
+    rng = np.random.default_rng(8)
+    blocks = [0.7 * squeezed(rng.uniform(0.2, 1.0), rng.uniform(0, 3)) + 0.3 * np.eye(2) for _ in range(4)]
+    V = xxpp_from_blocks(blocks)
+    m = rng.normal(0, 0.8, 8)
+    singles = [oracle.p0_displaced(V, m, [k]) for k in range(4)]
+    for S in ([0, 1], [1, 2, 3], [0, 1, 2, 3]):
+        assert oracle.p0_displaced(V, m, S) == pytest.approx(np.prod([singles[k] for k in S]), rel=1e-13)
+    inst = synthetic.random_instance(6, 3, seed=17)
+    for S in ([0], [1, 4], [0, 2, 5]):
+        assert oracle.p0_displaced(inst.V, np.zeros(12), S) == pytest.approx(oracle.p0(inst.V, S), rel=1e-13)
+    e = oracle.entries_displaced(V, m, np.array([[0, 1, 2]]))
+    assert abs(e["kappa"][0]) < 1e-14  # independent modes: no joint cumulant
+
+
+def test_displaced_thermal_closed_form():
+    """Displaced thermal state: V = (2 nbar + 1) I, mean (x, p): the vacuum probability
+    is exp(-(x^2 + p^2) / (4 (nbar + 1))) / (nbar + 1)."""
+    for nbar, x, p in ((0.5, 1.0, -0.3), (2.0, -2.2, 0.7)):
+        V = (2 * nbar + 1) * np.eye(2)
+        want = np.exp(-(x * x + p * p) / (4 * (nbar + 1))) / (nbar + 1)
+        assert oracle.p0_displaced(V, np.array([x, p]), [0]) == pytest.approx(want, rel=1e-14)
+
+
+def _fock_two_mode_state(cut, r1, a1, r2, a2, theta, phi):
+    """Two displaced squeezed vacua mixed on a beam splitter, built in a truncated
+    Fock space by matrix exponentials of the ladder operators (no Gaussian
+    formalism involved). Returns the state and the ladder operators."""
+    from scipy.linalg import expm
+    a = np.diag(np.sqrt(np.arange(1, cut)), 1).astype(complex)
+    one = np.eye(cut)
+
+    def mode(r, alpha):
+        sq = expm(0.5 * r * (a @ a - a.conj().T @ a.conj().T))
+        disp = expm(alpha * a.conj().T - np.conj(alpha) * a)
+        v = np.zeros(cut, complex); v[0] = 1
+        return disp @ sq @ v
+
+    A, B = np.kron(a, one), np.kron(one, a)
+    bs = expm(theta * (np.exp(1j * phi) * A.conj().T @ B - np.exp(-1j * phi) * A @ B.conj().T))
+    psi = bs @ np.kron(mode(r1, a1), mode(r2, a2))
+    return psi.reshape(cut, cut), (A, B)
+
+
+def test_displaced_two_mode_state_matches_fock_space():
+    """Eq. vacuum_gaussian_prob with first moments, against a state vector in Fock
+    space: mean and covariance are measured from the state (x = a + a^dag,
+    p = -i(a - a^dag), hbar = 2), vacuum probabilities are the squared amplitudes."""
+    cut = 34
+    psi, (A, B) = _fock_two_mode_state(cut, 0.35, 0.5 - 0.3j, 0.2, -0.4 + 0.2j, 0.7, 0.4)
+    vec = psi.reshape(-1)
+    quads = [A + A.conj().T, B + B.conj().T, -1j * (A - A.conj().T), -1j * (B - B.conj().T)]
+    ev = lambda op: np.vdot(vec, op @ vec)
+    m = np.array([ev(q).real for q in quads])
+    V = np.array([[(0.5 * ev(qa @ qb + qb @ qa)).real - m[i] * m[j] for j, qb in enumerate(quads)]
+                  for i, qa in enumerate(quads)])
+    prob = np.abs(psi) ** 2
+    assert oracle.p0_displaced(V, m, [0]) == pytest.approx(prob[0, :].sum(), rel=1e-9)
+    assert oracle.p0_displaced(V, m, [1]) == pytest.approx(prob[:, 0].sum(), rel=1e-9)
+    assert oracle.p0_displaced(V, m, [0, 1]) == pytest.approx(prob[0, 0], rel=1e-9)
+    e = oracle.entries_displaced(V, m, np.array([[0, 1]]))
+    click_both = prob.sum() - prob[0, :].sum() - prob[:, 0].sum() + prob[0, 0]
+    assert e["mu"][0] == pytest.approx(click_both, rel=1e-9)
+    q0, q1 = 1 - prob[0, :].sum(), 1 - prob[:, 0].sum()
+    assert e["kappa"][0] == pytest.approx(click_both - q0 * q1, abs=1e-10)
+
+
+def test_displaced_squeezed_single_mode_closed_form():
+    """D(alpha) S(r)|0> with x squeezed (V = diag(e^{-2r}, e^{2r})): the Fock-basis
+    overlap gives |<0|D S|0>|^2 = exp(-|alpha|^2 - tanh r Re(conj(alpha)^2)) / cosh r."""
+    for r, alpha in ((0.4, 0.6 + 0.2j), (1.1, -0.3 + 0.9j), (0.0, 1.2j)):
+        V = np.diag([np.exp(-2 * r), np.exp(2 * r)])
+        m = np.array([2 * alpha.real, 2 * alpha.imag])
+        want = np.exp(-abs(alpha) ** 2 - tanh(r) * (np.conj(alpha) ** 2).real) / cosh(r)
+        assert oracle.p0_displaced(V, m, [0]) == pytest.approx(want, rel=1e-13)
