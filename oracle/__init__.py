@@ -63,6 +63,8 @@ def _load():
     lib.orc_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D]; lib.orc_tables.restype = ctypes.c_int
     lib.orc_grad.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_grad.restype = ctypes.c_int
     lib.orc_spin_tables.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]; lib.orc_spin_tables.restype = ctypes.c_int
+    lib.orc_spin_tables_from_p0.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D]
+    lib.orc_spin_tables_from_p0.restype = ctypes.c_int
     lib.orc_p0_displaced.argtypes = [D, D, ctypes.c_int, I, ctypes.c_int]; lib.orc_p0_displaced.restype = ctypes.c_double
     lib.orc_entries_displaced.argtypes = [D, D, ctypes.c_int, ctypes.c_int, I, ctypes.c_int64, D, D, D]
     lib.orc_entries_displaced.restype = None
@@ -221,6 +223,18 @@ def spin_tables(V, kmax: int):
     c, k = np.empty(N), np.empty(N)
     if _load().orc_spin_tables(_dp(V), M, kmax, _dp(c), _dp(k)) != 0:
         raise ValueError("orc_spin_tables rejected its arguments")
+    return c, k
+
+
+def spin_tables_displaced(V, mean, kmax: int):
+    """(c, kappa) of a displaced state: the spin tables over its P0 table."""
+    V = _V(V)
+    M = V.shape[0] // 2
+    p0 = tables_displaced(V, mean, kmax)[0]
+    N = table_size(M, kmax)
+    c, k = np.empty(N), np.empty(N)
+    if _load().orc_spin_tables_from_p0(_dp(np.ascontiguousarray(p0)), M, kmax, _dp(c), _dp(k)) != 0:
+        raise ValueError("orc_spin_tables_from_p0 rejected its arguments")
     return c, k
 
 

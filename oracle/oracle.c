@@ -425,12 +425,25 @@ int orc_tables(const double *V, int M, int kmax, double *p0_out, double *mu_out,
    correlator_sum_cov over the P0 entries of the subsets of S, kappa(S) by Eq.
    cumulant_corr_main over the c entries of the blocks of S. Either output may be
    NULL. Returns 0, or -1 on bad args. */
+int orc_spin_tables_from_p0(const double *p0, int M, int kmax, double *c_out, double *k_out);
+
 int orc_spin_tables(const double *V, int M, int kmax, double *c_out, double *k_out) {
     if (M <= 0 || kmax <= 0 || kmax > M || kmax > ORC_MAXD) return -1;
     uint64_t N = table_offset(M, kmax + 1);
     double *p0 = (double *)malloc(sizeof(double) * N);
-    double *c = c_out ? c_out : (double *)malloc(sizeof(double) * N);
     orc_tables(V, M, kmax, p0, NULL, NULL);
+    int rc = orc_spin_tables_from_p0(p0, M, kmax, c_out, k_out);
+    free(p0);
+    return rc;
+}
+
+/* The same two tables from a given P0 table. Expanding prod_k (-1)^{x_k} =
+   prod_k (2 y_k - 1) over the no-click indicators y_k, whose joint moments are
+   the P0 entries, gives Eq. correlator_sum_cov for any state, displaced or not. */
+int orc_spin_tables_from_p0(const double *p0, int M, int kmax, double *c_out, double *k_out) {
+    if (M <= 0 || kmax <= 0 || kmax > M || kmax > ORC_MAXD) return -1;
+    uint64_t N = table_offset(M, kmax + 1);
+    double *c = c_out ? c_out : (double *)malloc(sizeof(double) * N);
     for (int d = 1; d <= kmax; ++d) {
         int64_t cnt = (int64_t)orc_binom(M, d);
         int *sets = (int *)malloc(sizeof(int) * (size_t)cnt * d);
@@ -474,7 +487,6 @@ int orc_spin_tables(const double *V, int M, int kmax, double *c_out, double *k_o
             free(sets);
         }
     }
-    free(p0);
     if (!c_out) free(c);
     return 0;
 }

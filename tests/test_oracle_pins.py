@@ -502,3 +502,33 @@ def test_displaced_squeezed_single_mode_closed_form():
         m = np.array([2 * alpha.real, 2 * alpha.imag])
         want = np.exp(-abs(alpha) ** 2 - tanh(r) * (np.conj(alpha) ** 2).real) / cosh(r)
         assert oracle.p0_displaced(V, m, [0]) == pytest.approx(want, rel=1e-13)
+
+
+def test_displaced_tables_consistent_with_fock_space_and_spin_identity():
+    """Displaced tables: the spin correlator of the two-mode Fock-space state is
+    E[(-1)^{x_0 + x_1}] summed from its photon-number distribution, and the spin
+    cumulants of order >= 2 are (-2)^{|S|} times the click cumulants
+    (Eq. cumulant_exponential)."""
+    psi, _ = _fock_two_mode_state(34, 0.3, 0.2 + 0.4j, 0.25, -0.5, 0.9, -0.2)
+    vec = psi.reshape(-1)
+    cut = psi.shape[0]
+    a = np.diag(np.sqrt(np.arange(1, cut)), 1).astype(complex)
+    A, B = np.kron(a, np.eye(cut)), np.kron(np.eye(cut), a)
+    quads = [A + A.conj().T, B + B.conj().T, -1j * (A - A.conj().T), -1j * (B - B.conj().T)]
+    ev = lambda op: np.vdot(vec, op @ vec)
+    m = np.array([ev(q).real for q in quads])
+    V = np.array([[(0.5 * ev(qa @ qb + qb @ qa)).real - m[i] * m[j] for j, qb in enumerate(quads)]
+                  for i, qa in enumerate(quads)])
+    prob = np.abs(psi) ** 2
+    click0 = np.ones(cut); click0[0] = 0
+    s0 = 1 - 2 * click0  # (-1)^{x}: +1 for no click, -1 for a click
+    c, k = oracle.spin_tables_displaced(V, m, 2)
+    assert c[2] == pytest.approx(float(s0 @ prob @ s0), rel=1e-8)
+    assert c[0] == pytest.approx(float(s0 @ prob.sum(axis=1)), rel=1e-8)
+    inst = synthetic.random_instance(7, 3, seed=23)
+    mean = np.random.default_rng(3).normal(0, 0.6, 14)
+    _, _, kt = oracle.tables_displaced(inst.V, mean, 4)
+    _, kk = oracle.spin_tables_displaced(inst.V, mean, 4)
+    for d in range(2, 5):
+        o, n = oracle.table_size(7, d) - comb(7, d), comb(7, d)
+        np.testing.assert_allclose(kk[o:o + n], (-2.0) ** d * kt[o:o + n], rtol=1e-12, atol=1e-13)
