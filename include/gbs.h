@@ -144,6 +144,30 @@ int gbs_click_moments(const double *V, int M, int kmax, double *mu_out, int prec
 int gbs_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision,
                   void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- displaced states */
+
+/* Tables gbs_displaced_tables can fill. */
+typedef enum {
+    GBS_TABLE_P0 = 0,              /* P0(S), Eq. vacuum_gaussian_prob */
+    GBS_TABLE_CLICK_MOMENT = 1,    /* mu(S), Eq. joint_moments_def */
+    GBS_TABLE_CLICK_CUMULANT = 2,  /* kt(S), Eq. joint_cumulants_def */
+    GBS_TABLE_SPIN_CORRELATOR = 3, /* c(S) = E[prod_{k in S} (-1)^{x_k}] */
+    GBS_TABLE_SPIN_CUMULANT = 4    /* kappa(S), Eq. cumulant_corr_main */
+} gbs_table;
+
+/* One table of a DISPLACED Gaussian state: first moments mean[2M] (device, FP64,
+   xxpp: mean[k] = <x_k>, mean[k+M] = <p_k>, hbar = 2) and covariance V as for
+   the other entry points. The vacuum probabilities carry the exponential factor
+   of Eq. vacuum_gaussian_prob,
+     P0(S) = exp(-1/2 mean_S^T (V_S + I)^{-1} mean_S) / sqrt(det((V_S + I)/2)),
+   and the other tables follow from P0 exactly as in the zero-mean case (the
+   inclusion-exclusion and partition sums do not depend on the mean). With
+   mean = 0 the tables equal those of the zero-mean entry points at GBS_FP64.
+   Computed in FP64 (workspace: gbs_workspace_bytes(M, kmax, GBS_FP64)).
+   table: a gbs_table value. mean must be non-NULL. Errors as elsewhere. */
+int gbs_displaced_tables(const double *V, const double *mean, int M, int kmax, int table, double *out,
+                         void *workspace, size_t ws_bytes, void *cuda_stream);
+
 /* ---------------------------------------------------------------- schedule autotuning */
 
 /* Times gbs_cumulants for this (M, kmax, precision) under each candidate

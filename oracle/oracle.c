@@ -111,12 +111,19 @@ static void reduced_A(const double *V, int M, const int *T, int t, double *a) {
     }
 }
 
+/* 1 if every mode of T lies in [0, M). */
+static int modes_in_range(const int *T, int t, int M) {
+    for (int i = 0; i < t; ++i)
+        if (T[i] < 0 || T[i] >= M) return 0;
+    return 1;
+}
+
 /* ---------------------------------------------------------------- Eq. vacuum_gaussian_prob */
 
 double orc_p0(const double *V, int M, const int *T, int t) {
     double a[ORC_MAXN * ORC_MAXN];
     if (t == 0) return 1.0;
-    if (t > ORC_MAXD) return NAN;
+    if (t > ORC_MAXD || !modes_in_range(T, t, M)) return NAN;
     reduced_A(V, M, T, t, a);
     double det = det_lu(a, 2 * t);
     if (!(det > 0.0)) return NAN;
@@ -131,7 +138,7 @@ double orc_cumulant_from_moments(const double *mom, int d);
 double orc_p0_displaced(const double *V, const double *mean, int M, const int *T, int t) {
     double a[ORC_MAXN * ORC_MAXN], b[ORC_MAXN * ORC_MAXN], inv[ORC_MAXN * ORC_MAXN];
     if (t == 0) return 1.0;
-    if (t > ORC_MAXD) return NAN;
+    if (t > ORC_MAXD || !modes_in_range(T, t, M)) return NAN;
     int n = 2 * t;
     reduced_A(V, M, T, t, a);
     memcpy(b, a, sizeof(double) * n * n);

@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
         f.restype = i32
+    L.gbs_displaced_tables.argtypes = [vp, vp, i32, i32, i32, vp, vp, sz, vp]
+    L.gbs_displaced_tables.restype = i32
     _lib = L
     return L
 
@@ -183,6 +185,34 @@ def spin_correlators(V, kmax, precision="fp64", out=None, workspace=None, check=
 def spin_cumulants(V, kmax, precision="fp64", out=None, workspace=None, check=True):
     """Spin cumulants kappa(S) (the sampler's input table) for every 1 <= |S| <= kmax."""
     return _forward("gbs_spin_cumulants", V, kmax, precision, out, workspace, check)
+
+
+TABLES = {"p0": 0, "mu": 1, "kappa": 2, "spin_c": 3, "spin_kappa": 4}
+
+
+def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, check=True):
+    """One table ("p0", "mu", "kappa", "spin_c" or "spin_kappa") of a displaced
+    Gaussian state with first moments mean (2M, xxpp, hbar = 2), in FP64."""
+    V, M = _prep(V)
+    if table not in TABLES:
+        raise ValueError(f"table must be one of {sorted(TABLES)}")
+    mean = _dev64(mean, "mean")
+    if mean.numel() != 2 * M:
+        raise ValueError(f"mean must have 2M = {2 * M} entries")
+    n = table_size(M, kmax)
+    if n == 0:
+        raise GbsError(1, f"invalid (M={M}, kmax={kmax})")
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=V.device)
+    elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
+    ws = workspace or Workspace(M, kmax, "fp64", device=V.device)
+    st = torch.cuda.current_stream(V.device)
+    _check(lib().gbs_displaced_tables(_vp(V), _vp(mean), M, kmax, TABLES[table], _vp(out), ctypes.c_void_p(ws.ptr),
+                                      ws.nbytes, ctypes.c_void_p(st.cuda_stream)))
+    if check:
+        _check(ws.status(st))
+    return out
 
 
 def _vp(t: torch.Tensor):

@@ -77,17 +77,20 @@ int check_common(const double *V, int M, int kmax, const void *out, int precisio
 }
 
 int run_forward(int mode, const double *V, int M, int kmax, double *out, int precision, void *ws, size_t ws_bytes,
-                void *stream) {
+                void *stream, const double *mean = nullptr) {
     gbs::WsLayout L;
     int sms = 0;
     int rc = check_common(V, M, kmax, out, precision, ws, ws_bytes, L, sms);
     if (rc != GBS_OK) return rc;
+    if (mean && (((uintptr_t)mean & 7) || !is_device_ptr(mean)))
+        return fail(GBS_ERR_INVALID_ARG, "mean must be 8-byte aligned CUDA device (or managed) memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *w = static_cast<char *>(ws);
     cudaError_t e = cudaMemsetAsync(w + L.status_off, 0, 256, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     gbs::FwdArgs a{};
     a.V = V;
+    a.mean = mean;
     a.M = M;
     a.kmax = kmax;
     a.mode = mode;
@@ -117,7 +120,7 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
         a.ev = g_ev;
         g_timing_used = true;
     }
-    e = gbs::launch_forward(a, st);
+    e = mean ? gbs::launch_forward_displaced(a, st) : gbs::launch_forward(a, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     return ok();
 }
@@ -401,6 +404,18 @@ int gbs_spin_correlators(const double *V, int M, int kmax, double *c_out, int pr
 int gbs_spin_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
                        size_t ws_bytes, void *cuda_stream) {
     return run_forward(gbs::MODE_SPINK, V, M, kmax, kappa_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+int gbs_displaced_tables(const double *V, const double *mean, int M, int kmax, int table, double *out,
+                         void *workspace, size_t ws_bytes, void *cuda_stream) {
+    if (!mean) return fail(GBS_ERR_INVALID_ARG, "mean must be non-NULL (use the zero-mean entry points otherwise)");
+    if (table < GBS_TABLE_P0 || table > GBS_TABLE_SPIN_CUMULANT)
+        return fail(GBS_ERR_INVALID_ARG, "table must be one of the gbs_table values; got %d", table);
+    static_assert(GBS_TABLE_P0 == gbs::MODE_P0 && GBS_TABLE_CLICK_MOMENT == gbs::MODE_MU &&
+                      GBS_TABLE_CLICK_CUMULANT == gbs::MODE_KAPPA && GBS_TABLE_SPIN_CORRELATOR == gbs::MODE_SPINC &&
+                      GBS_TABLE_SPIN_CUMULANT == gbs::MODE_SPINK,
+                  "table numbering follows the kernel modes");
+    return run_forward(table, V, M, kmax, out, GBS_FP64, workspace, ws_bytes, cuda_stream, mean);
 }
 
 }  // extern "C"

@@ -153,6 +153,36 @@ __device__ __forceinline__ Blk ablk(const double *A, int M, int x, int y) {
     return load_blk(A + 4 * ((size_t)x * M + y));
 }
 
+// ---------------------------------------------------------------- first moments
+// Displaced states: with b = mean / 2 per mode (b_k = (mean[k], mean[k+M]) / 2),
+// the exponent of Eq. vacuum_gaussian_prob (hbar = 2) is
+// -1/2 mean^T (V + I)^{-1} mean = -b^T A^{-1} b. Under the elimination of a pivot
+// p with inverse factor m_p, a mode x's reduced half-mean becomes
+// b(x) - y(x)^T g_p, y(x) = m_p A[p, x], g_p = m_p b(p); the leaf j left after
+// eliminating S' contributes r^T Sch_j^{-1} r with r its reduced half-mean.
+struct Vec2 {
+    double v0, v1;
+};
+
+__device__ __forceinline__ Vec2 half_mean(const double *mean, int M, int k) {
+    return Vec2{0.5 * mean[k], 0.5 * mean[k + M]};
+}
+
+// m * b for an inverse Cholesky factor m.
+__device__ __forceinline__ Vec2 lvec(const LInv &m, const Vec2 &b) {
+    return Vec2{m.m00 * b.v0, fma(m.m10, b.v0, m.m11 * b.v1)};
+}
+
+// r - w^T g for a 2x2 block w (rows = pivot components).
+__device__ __forceinline__ Vec2 sub_wtg(const Vec2 &r, const Blk &w, const Vec2 &g) {
+    return Vec2{fma(-w.a10, g.v1, fma(-w.a00, g.v0, r.v0)), fma(-w.a11, g.v1, fma(-w.a01, g.v0, r.v1))};
+}
+
+// r^T S^{-1} r for a 2x2 SPD block S, given 1 / det S.
+__device__ __forceinline__ double quad_inv(const Sym &s, double idet, const Vec2 &r) {
+    return idet * fma(s.s11 * r.v0, r.v0, fma(-2.0 * s.s01 * r.v0, r.v1, s.s00 * r.v1 * r.v1));
+}
+
 __device__ __forceinline__ void flag_status(unsigned *status, unsigned bits) {
     if (status) atomicOr(status, bits);
 }

@@ -15,6 +15,7 @@ enum Mode : int { MODE_P0 = 0, MODE_MU = 1, MODE_KAPPA = 2, MODE_SPINC = 3, MODE
 // gbs.h (order groups, colex ranks within an order).
 struct FwdArgs {
     const double *V;      // 2M x 2M covariance (row-major, xxpp)
+    const double *mean;   // first moments (2M, xxpp) of a displaced state; nullptr = zero mean
     int M, kmax, mode, precision;
     double *A;            // packed 2x2 blocks of (V+I)/2, M*M*4 doubles (workspace)
     float *Af;            // the same blocks as float pairs (hi x4, lo x4), refined path (workspace)
@@ -51,7 +52,11 @@ struct WsLayout {
 // shape; with one, only the 512-thread shape runs, one CTA per multiprocessor).
 WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 3);
 
+// Queues the packing of A = (V+I)/2 into 2x2 blocks.
+cudaError_t launch_pack(const FwdArgs &a, cudaStream_t stream);
 // Queues every kernel of one forward call on stream; returns a cudaError_t.
 cudaError_t launch_forward(const FwdArgs &a, cudaStream_t stream);
+// The same for a displaced state (a.mean set, a.precision = 0).
+cudaError_t launch_forward_displaced(const FwdArgs &a, cudaStream_t stream);
 
 }  // namespace gbs

@@ -1,0 +1,177 @@
+// Launch plumbing of the forward kernels, shared by the zero-mean translation
+// unit (gbs_fwd.cu) and the displaced-state one (gbs_disp.cu): the per-order
+// kernels, the persistent prefix-tree kernel and its launcher, each templated on
+// DISP (first moments carried through the elimination, FP64 only).
+#pragma once
+#include "gbs_tree.cuh"
+
+namespace gbs {
+
+template <int MODE, bool DISP>
+__global__ void order1_kernel(FwdArgs a, bool write_p0) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < a.M) order1_entry<MODE, DISP>(a, j, write_p0);
+}
+
+template <int MODE, bool DISP>
+__global__ void order2_kernel(FwdArgs a, bool write_p0) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < binom2(a.M)) order2_entry<MODE, DISP>(a, t, write_p0);
+}
+
+template <int MODE, bool DISP>
+__global__ void order3_kernel(FwdArgs a, bool write_p0) {
+    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < binom(a.M, 3)) order3_entry<MODE, DISP>(a, r, write_p0);
+}
+
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
+__global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
+    using SH = TreeShared<D, XC, DISP>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH &sh = *reinterpret_cast<SH *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int M = a.M;
+    const int c4hi = c4_max<D>(M);
+    const int K = c4hi - 2;  // c4 runs c4hi, c4hi-1, .., 3
+    double *const slot = a.scratch + (size_t)blockIdx.x * a.slot_doubles;
+
+    // prefix of item counts over c4 in descending order (warp 0, chunked scan)
+    if (tid < 32) {
+        const int per = (K + 31) / 32;
+        const int lo = tid * per, hi = min(K, lo + per);
+        uint32_t sum = 0;
+        for (int k = lo; k < hi; ++k) sum += items_for_c4<D>(M, c4hi - k, target);
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (int k = lo; k < hi; ++k) {
+            sh.c4pref[k] = run;
+            run += items_for_c4<D>(M, c4hi - k, target);
+        }
+        if (tid == 31) sh.c4pref[K] = incl;
+    }
+    __syncthreads();
+    const uint32_t total_items = sh.c4pref[K];
+
+    for (;;) {
+        if (tid == 0) sh.item = atomicAdd(a.counters + D, 1u);
+        __syncthreads();
+        const uint32_t item = sh.item;
+        if (item >= total_items) break;
+        // decode item -> (c4, c5, class s of nc)
+        int lo = 0, hi = K;  // find k with c4pref[k] <= item < c4pref[k+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sh.c4pref[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c4 = c4hi - lo;
+        const int nc = n_classes(c4, target);
+        const uint32_t rr = item - sh.c4pref[lo];
+        const int u = (int)(rr / nc), s = (int)(rr % nc);
+        const int c5 = (D == 5) ? c4 + 1 + u : M;
+        tree_item<D, MODE, PREC, NT, XC, DISP>(a, sh, slot, c4, c5, s, nc, write_p0, a.ccap);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
+static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
+    const int M = a.M;
+    const uint64_t leaves = binom(M, D);
+    if (leaves == 0) return cudaSuccess;
+    const size_t smem = sizeof(TreeShared<D, XC, DISP>);
+    auto fn = tree_kernel<D, MODE, PREC, NT, XC, MINB, DISP>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid_max = a.sms * per_sm;
+    if (grid_max > a.slots) grid_max = a.slots;
+    const int grain = a.grain > 0 ? a.grain : kDefaultCfg.grain;
+    uint64_t target = leaves / ((uint64_t)grain * (uint64_t)grid_max);
+    if (target < 256) target = 256;
+    uint64_t items = 0;
+    for (int c4 = c4_max<D>(M); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, target);
+    if (items == 0) return cudaSuccess;
+    const int grid = (int)(items < (uint64_t)grid_max ? items : (uint64_t)grid_max);
+    fn<<<grid, NT, smem, st>>>(a, target, write_p0);
+    return cudaGetLastError();
+}
+
+template <int D, int MODE, int PREC, bool DISP>
+static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t st) {
+    FwdArgs a = a_in;  // unset (zero) schedule fields take the defaults
+    if (a.grain <= 0) a.grain = kDefaultCfg.grain;
+    if (a.ccap <= 0 || a.ccap > CCAP) a.ccap = kDefaultCfg.ccap;
+    if constexpr (DISP) {
+        // displaced states: FP64, one 512-thread CTA per multiprocessor
+        return launch_tree_v<D, MODE, 0, TREE_THREADS, XCAP, 1, true>(a, write_p0, st);
+    } else {
+        if (a.variant == 1 && a.M <= kVariant1MaxM)
+            return launch_tree_v<D, MODE, PREC, 256, 576, 2, false>(a, write_p0, st);
+        if constexpr (PREC == 1) {
+            // register-lean refined kernels: 20 warps in one CTA, or 3 CTAs of 8 warps
+            if (a.variant == 2) return launch_tree_v<D, MODE, PREC, 640, XCAP, 1, false>(a, write_p0, st);
+            if (a.variant == 3 && a.M <= kVariant1MaxM)
+                return launch_tree_v<D, MODE, PREC, 256, 576, 3, false>(a, write_p0, st);
+        }
+        return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP, 1, false>(a, write_p0, st);
+    }
+}
+
+template <int MODE, bool DISP>
+static cudaError_t launch_mode(const FwdArgs &a, cudaStream_t st) {
+    const int M = a.M;
+    auto wp = [&](int d) { return MODE == MODE_P0 || d < a.kmax; };
+    auto mark = [&](int i) {
+        if (a.ev) cudaEventRecord(a.ev[i], st);
+    };
+    cudaError_t e = cudaSuccess;
+    order1_kernel<MODE, DISP><<<(M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(a, wp(1));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(2);
+    if (a.kmax >= 2) {
+        const uint64_t n2 = binom2(M);
+        order2_kernel<MODE, DISP><<<(unsigned)((n2 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(2));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mark(3);
+    if (a.kmax >= 3) {
+        const uint64_t n3 = binom(M, 3);
+        order3_kernel<MODE, DISP><<<(unsigned)((n3 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(3));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mark(4);
+    if (a.kmax >= 4) {
+        e = a.precision == 0 ? launch_tree<4, MODE, 0, DISP>(a, wp(4), st) : launch_tree<4, MODE, 1, DISP>(a, wp(4), st);
+        if (e != cudaSuccess) return e;
+    }
+    mark(5);
+    if (a.kmax >= 5) {
+        e = a.precision == 0 ? launch_tree<5, MODE, 0, DISP>(a, wp(5), st) : launch_tree<5, MODE, 1, DISP>(a, wp(5), st);
+        if (e != cudaSuccess) return e;
+    }
+    mark(6);
+    return cudaSuccess;
+}
+
+// Queues the per-order kernels (orders 1..kmax) of one forward call after packing.
+template <bool DISP>
+cudaError_t launch_orders(const FwdArgs &a, cudaStream_t st) {
+    switch (a.mode) {
+        case MODE_P0: return launch_mode<MODE_P0, DISP>(a, st);
+        case MODE_MU: return launch_mode<MODE_MU, DISP>(a, st);
+        case MODE_SPINC: return launch_mode<MODE_SPINC, DISP>(a, st);
+        case MODE_SPINK: return launch_mode<MODE_SPINK, DISP>(a, st);
+        default: return launch_mode<MODE_KAPPA, DISP>(a, st);
+    }
+}
+
+}  // namespace gbs

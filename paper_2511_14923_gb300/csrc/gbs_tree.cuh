@@ -128,11 +128,13 @@ __device__ __forceinline__ void pack_entry(const double *__restrict__ V, int M, 
 }
 
 
-template <int MODE>
+template <int MODE, bool DISP = false>
 __device__ __forceinline__ void order1_entry(const FwdArgs &a, int j, bool write_p0) {
     const Sym s = blk_sym(ablk(a.A, a.M, j, j));
     const double det = det_sym(s);
-    double P0 = rsqrt(det);
+    const double rs = rsqrt(det);
+    double P0 = rs;
+    if (DISP) P0 *= exp(-quad_inv(s, rs * rs, half_mean(a.mean, a.M, j)));
     if (!(det > 0.0) || !(s.s00 > 0.0)) {
         flag_status(a.status, ST_NOT_POSDEF);
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
@@ -144,7 +146,7 @@ __device__ __forceinline__ void order1_entry(const FwdArgs &a, int j, bool write
 }
 
 
-template <int MODE>
+template <int MODE, bool DISP = false>
 __device__ __forceinline__ void order2_entry(const FwdArgs &a, uint32_t t, bool write_p0) {
     const int M = a.M;
     int c2, j;
@@ -155,7 +157,12 @@ __device__ __forceinline__ void order2_entry(const FwdArgs &a, uint32_t t, bool 
     const Blk w = lmul(m2, ablk(a.A, M, c2, j));
     const Sym sch = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), w);
     const double det2 = det_sym(sch);
-    double P0 = a.p0[c2] * rsqrt(det2);
+    const double rs = rsqrt(det2);
+    double P0 = a.p0[c2] * rs;
+    if (DISP) {
+        const Vec2 r = sub_wtg(half_mean(a.mean, M, j), w, lvec(m2, half_mean(a.mean, M, c2)));
+        P0 *= exp(-quad_inv(sch, rs * rs, r));
+    }
     if (!(det2 > 0.0) || !ok) {
         flag_status(a.status, ST_NOT_POSDEF);
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
@@ -170,7 +177,7 @@ __device__ __forceinline__ void order2_entry(const FwdArgs &a, uint32_t t, bool 
 }
 
 
-template <int MODE>
+template <int MODE, bool DISP = false>
 __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool write_p0) {
     const int M = a.M;
     int s[3];
@@ -185,12 +192,20 @@ __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool 
     const LInv m2 = chol2_inv(sym_sub_gram(blk_sym(ablk(a.A, M, c2, c2)), z2), ok2, dd);
     const Sym dj = sym_sub_gram(blk_sym(ablk(a.A, M, j, j)), zj);
     const Blk X = blk_sub_cross(ablk(a.A, M, c2, j), z2, zj);
-    const Sym sch = sym_sub_gram(dj, lmul(m2, X));
+    const Blk w = lmul(m2, X);
+    const Sym sch = sym_sub_gram(dj, w);
     const double det2 = det_sym(sch);
     uint64_t baseJ[2], baseT[2], idxQ[2];
     const int P[1] = {c3};
     child_bases<1>(P, M, baseJ, baseT, idxQ);
-    double P0 = a.p0[baseJ[1] + c2] * rsqrt(det2);
+    const double rs = rsqrt(det2);
+    double P0 = a.p0[baseJ[1] + c2] * rs;
+    if (DISP) {
+        const Vec2 g3 = lvec(m3, half_mean(a.mean, M, c3));
+        const Vec2 r2 = sub_wtg(half_mean(a.mean, M, c2), z2, g3);
+        const Vec2 rj = sub_wtg(half_mean(a.mean, M, j), zj, g3);
+        P0 *= exp(-quad_inv(sch, rs * rs, sub_wtg(rj, w, lvec(m2, r2))));
+    }
     if (!(det2 > 0.0) || !ok3 || !ok2) {
         flag_status(a.status, ST_NOT_POSDEF);
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
@@ -205,15 +220,15 @@ __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool 
 
 // ---------------------------------------------------------------- tree kernel
 
-template <int D, int XC = XCAP>
+template <int D, int XC = XCAP, bool DISP = false>
 struct TreeShared {
     static constexpr int NP = D - 2;       // |P|
     static constexpr int NQ = 1 << NP;     // subsets of P
     // item decode
     uint32_t c4pref[GBS_MAX_MODES + 2];
     uint32_t item;
-    // uniform pivots of the item's U
-    double upiv[8];
+    // uniform pivots of the item's U (and, displaced, their whitened half-means)
+    double upiv[DISP ? 10 : 8];
     // children of the current batch
     int c3[CCAP];
     int xoff[CCAP + 1];
@@ -223,14 +238,19 @@ struct TreeShared {
     double p0R[CCAP][NQ];
     double m3[CCAP][3];
     float m3f[CCAP][6];  // refined path: m3 as float pairs (h, l) x 3
+    double g3[DISP ? CCAP : 1][2];  // displaced: whitened half-mean of each child's c3 pivot
     // Per x-entry data, structure of arrays. FP64 path (10 double rows):
     // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
     // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (23 float
     // rows): z hi/lo (0-3, 4-7), d hi/lo (8-10, 11-13), c2 pivot: FP32 factor
     // l (14-16), its inverse m (17-19), residual d - l l^T (20-22).
+    // Displaced states add 4 double rows: the reduced half-mean r(x) after
+    // eliminating U and c3 (rows 10-11) and its whitened form g2(x) = m2(x) r(x)
+    // as a c2 pivot (rows 12-13).
     // Before the batches of an item start, the same storage holds Y(x) of the
     // elimination of U (8 doubles per mode x < c4).
-    static constexpr int XBYTES = (23 * 4 > 10 * 8 ? 23 * 4 : 10 * 8) * XC;
+    static constexpr int XROWS = DISP ? 14 : 10;
+    static constexpr int XBYTES = (23 * 4 > XROWS * 8 ? 23 * 4 : XROWS * 8) * XC;
     alignas(16) unsigned char xraw[XBYTES];
     __device__ double (*xe())[XC] { return reinterpret_cast<double(*)[XC]>(xraw); }
     __device__ float (*xf())[XC] { return reinterpret_cast<float(*)[XC]>(xraw); }
@@ -306,11 +326,16 @@ __host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_
 // One work item of the prefix-tree kernel: U = {c4, c5} (D = 5) or {c4} (D = 4),
 // children c3 = c4-1-s, c4-1-s-nc, ... >= 2 (stride class s of nc). Called by all
 // threads of the block; sh is the block's shared memory, slot its scratch slot.
-template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP>
-__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &sh, double *const slot, const int c4,
-                                          const int c5, const int s, const int nc, const bool write_p0,
+//
+// Displaced states (DISP, FP64 only) carry the reduced half-means along: the
+// slot holds r_U(x) after the Schur blocks, the x-entries r(x) and g2(x), and
+// each leaf multiplies its P0 by exp(-r^T Sch^{-1} r).
+template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false>
+__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DISP> &sh, double *const slot,
+                                          const int c4, const int c5, const int s, const int nc, const bool write_p0,
                                           const int ccap = CCAP) {
-    using SH = TreeShared<D, XC>;
+    static_assert(!DISP || PREC == 0, "displaced states run in FP64");
+    using SH = TreeShared<D, XC, DISP>;
     constexpr int NP = SH::NP;
     constexpr int NQ = SH::NQ;
     constexpr int PALL = NQ - 1;
@@ -319,6 +344,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
     const int tid = threadIdx.x;
     const int M = a.M;
     double *const sdiag = slot + 4 * binom2(M);
+    double *const rU = sdiag + 4 * (size_t)M;  // displaced: reduced half-means, 2 per mode
     const double *__restrict__ A = a.A;
 
     // ---- Schur complement of A after eliminating U, modes < c4 -> slot
@@ -338,6 +364,15 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
         if (!ok || !ok2) flag_status(a.status, ST_NOT_POSDEF);
         sh.upiv[0] = m5.m00; sh.upiv[1] = m5.m10; sh.upiv[2] = m5.m11;
         sh.upiv[3] = m4.m00; sh.upiv[4] = m4.m10; sh.upiv[5] = m4.m11;
+        if constexpr (DISP) {
+            Vec2 g5{0, 0}, r4 = half_mean(a.mean, M, c4);
+            if (D == 5) {
+                g5 = lvec(m5, half_mean(a.mean, M, c5));
+                r4 = sub_wtg(r4, y5c4, g5);
+            }
+            const Vec2 g4 = lvec(m4, r4);
+            sh.upiv[6] = g5.v0; sh.upiv[7] = g5.v1; sh.upiv[8] = g4.v0; sh.upiv[9] = g4.v1;
+        }
     }
     __syncthreads();
     {
@@ -357,6 +392,13 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                 r4 = blk_sub_cross(r4, y5c4, y5);
             }
             const Blk y4 = lmul(m4, r4);
+            if constexpr (DISP) {
+                Vec2 r = half_mean(a.mean, M, x);
+                if (D == 5) r = sub_wtg(r, y5, Vec2{sh.upiv[6], sh.upiv[7]});
+                r = sub_wtg(r, y4, Vec2{sh.upiv[8], sh.upiv[9]});
+                rU[2 * x] = r.v0;
+                rU[2 * x + 1] = r.v1;
+            }
             const double v[8] = {y5.a00, y5.a01, y5.a10, y5.a11, y4.a00, y4.a01, y4.a10, y4.a11};
             if (PREC == 0) {
 #pragma unroll
@@ -461,6 +503,11 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
             const LInv m3 = chol2_inv(p3, ok, dd);
             if (!ok) flag_status(a.status, ST_NOT_POSDEF);
             sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
+            if constexpr (DISP) {
+                const Vec2 g3 = lvec(m3, Vec2{rU[2 * c3], rU[2 * c3 + 1]});
+                sh.g3[b][0] = g3.v0;
+                sh.g3[b][1] = g3.v1;
+            }
             if (PREC == 1) {
                 split_df(m3.m00, sh.m3f[b][0], sh.m3f[b][1]);
                 split_df(m3.m10, sh.m3f[b][2], sh.m3f[b][3]);
@@ -485,12 +532,21 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                 const Sym dx = sym_sub_gram(slot_diag_f64<PREC>(sdiag, x), z);
                 xe[0][e] = z.a00; xe[1][e] = z.a01; xe[2][e] = z.a10; xe[3][e] = z.a11;
                 xe[4][e] = dx.s00; xe[5][e] = dx.s01; xe[6][e] = dx.s11;
+                Vec2 r3{0, 0};
+                if constexpr (DISP) {
+                    r3 = sub_wtg(Vec2{rU[2 * x], rU[2 * x + 1]}, z, Vec2{sh.g3[b][0], sh.g3[b][1]});
+                    xe[10][e] = r3.v0; xe[11][e] = r3.v1;
+                }
                 if (x >= 1) {
                     bool ok;
                     double dd;
                     const LInv m2 = chol2_inv(dx, ok, dd);
                     if (!ok) flag_status(a.status, ST_NOT_POSDEF);
                     xe[7][e] = m2.m00; xe[8][e] = m2.m10; xe[9][e] = m2.m11;
+                    if constexpr (DISP) {
+                        const Vec2 g2 = lvec(m2, r3);
+                        xe[12][e] = g2.v0; xe[13][e] = g2.v1;
+                    }
                 }
             } else {
                 // z(x) = m3 S_U[c3, x] and d(x) = S_U[x, x] - z^T z in float pairs (FP32 pipe)
@@ -556,9 +612,15 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC> &s
                 const LInv m2{xe[7][e2], xe[8][e2], xe[9][e2]};
                 const Sym dj{xe[4][ej], xe[5][ej], xe[6][ej]};
                 const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
-                const Sym sch = sym_sub_gram(dj, lmul(m2, X));
+                const Blk w = lmul(m2, X);
+                const Sym sch = sym_sub_gram(dj, w);
                 const double det2 = det_sym(sch);
-                P0 = P0Sp * rsqrt(det2);
+                const double rs = rsqrt(det2);
+                P0 = P0Sp * rs;
+                if constexpr (DISP) {
+                    const Vec2 r = sub_wtg(Vec2{xe[10][ej], xe[11][ej]}, w, Vec2{xe[12][e2], xe[13][e2]});
+                    P0 *= exp(-quad_inv(sch, rs * rs, r));
+                }
                 ok = det2 > 0.0;
             } else {
                 const float4 *fs = reinterpret_cast<const float4 *>(slot) + 2 * (size_t)t;

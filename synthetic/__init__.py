@@ -142,3 +142,13 @@ def random_subsets(M: int, d: int, n: int, seed: int) -> np.ndarray:
         out[todo[ok]] = draw[ok]
         todo = todo[~ok]
     return out
+
+
+def displaced_mean(inst: Instance, seed: int, alpha_scale: float = 0.5) -> np.ndarray:
+    """First moments (2M, xxpp, hbar = 2) of the instance's network fed with coherent
+    displacements alpha_k ~ alpha_scale * (N(0,1) + i N(0,1)) / sqrt(2) on its inputs:
+    the output amplitudes are sqrt(eta) * (U alpha), and mean = 2 (Re, Im) of them."""
+    rng = np.random.default_rng(seed)
+    alpha = alpha_scale * (rng.standard_normal(inst.M) + 1j * rng.standard_normal(inst.M)) / np.sqrt(2.0)
+    beta = np.sqrt(inst.eta) * (inst.U @ alpha)
+    return np.concatenate([2.0 * beta.real, 2.0 * beta.imag])
