@@ -443,10 +443,16 @@ BwdLayout bwd_layout(int M, int kmax, int sms) {
     off += ((sizeof(double) * order_offset(M, kmax) + 255) & ~(size_t)255);
     b.gp0_off = off;
     off += ((sizeof(double) * N + 255) & ~(size_t)255);
-    // inverses of A_{T'} for the largest prefix order kmax - 1 (reused per order)
-    const int dp = kmax - 1;
+    // inverses of A_{T'} for one prefix order at a time (orders 1..kmax-1 reuse the
+    // region), sized for the order that needs the most: C(M, dp) packed
+    // 2dp x 2dp lower triangles, which for small M is not always dp = kmax - 1
+    size_t inv_doubles = 0;
+    for (int dp = 1; dp < kmax; ++dp) {
+        const size_t n = (size_t)binom(M, dp) * (size_t)(dp * (2 * dp + 1));
+        if (n > inv_doubles) inv_doubles = n;
+    }
     b.inv_off = off;
-    if (dp >= 1) off += ((sizeof(double) * binom(M, dp) * (size_t)(dp * (2 * dp + 1)) + 255) & ~(size_t)255);
+    off += ((sizeof(double) * inv_doubles + 255) & ~(size_t)255);
     b.total = off;
     return b;
 }
