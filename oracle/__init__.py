@@ -24,15 +24,16 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "sampler.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so with gcc (OpenMP if available)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile oracle.c and sampler.c into liboracle.so with gcc (OpenMP if available)."""
+    if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
-    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *_SRCS, "-o", _LIB + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -69,6 +70,9 @@ def _load():
     lib.orc_entries_displaced.argtypes = [D, D, ctypes.c_int, ctypes.c_int, I, ctypes.c_int64, D, D, D]
     lib.orc_entries_displaced.restype = None
     lib.orc_num_threads.argtypes = []; lib.orc_num_threads.restype = ctypes.c_int
+    U8 = ctypes.POINTER(ctypes.c_uint8)
+    lib.orc_sample_batch.argtypes = [D, ctypes.c_int, ctypes.c_int, I, ctypes.c_int64, D, U8, U8, D, D]
+    lib.orc_sample_batch.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -329,3 +333,32 @@ def chain_to_params(G: np.ndarray, r: np.ndarray, eta: np.ndarray, U: np.ndarray
             tot -= G[a, a]
         deta[m] = tot
     return dr, deta
+
+
+# ------------------------------------------------------------------ stage 2: chain-rule sampler
+
+def sample(kappa, M: int, K: int, u=None, force=None, orders=None):
+    """Chain-rule sampler (sampler.c): K = 3 single elision or K = 5 double
+    elision, reading the spin-cumulant table kappa (orders 1..K, table layout).
+    u: (ns, M) uniforms, or force: (ns, M) bits to score instead of drawing.
+    orders: (p+, p1, p2) expansion orders for K = 5 (default the paper's 3, 3, 2).
+    Returns (bits (ns, M) uint8, p (ns,) = estimated probability of each
+    bitstring, q0 (ns, M) = probability of a 0 each bit was drawn with)."""
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    assert kappa.size == table_size(M, K)
+    src = u if force is None else force
+    ns = np.asarray(src).reshape(-1, M).shape[0]
+    uu = None if u is None else np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(ns, M))
+    ff = None if force is None else np.ascontiguousarray(np.asarray(force, dtype=np.uint8).reshape(ns, M))
+    bits = np.empty((ns, M), dtype=np.uint8)
+    p = np.empty(ns)
+    q0 = np.empty((ns, M))
+    U8 = ctypes.POINTER(ctypes.c_uint8)
+    ordv = None if orders is None else np.ascontiguousarray(orders, dtype=np.int32)
+    bad = _load().orc_sample_batch(_dp(kappa), M, K, None if ordv is None else _ip(ordv), ns,
+                                   None if uu is None else _dp(uu),
+                                   None if ff is None else ff.ctypes.data_as(U8),
+                                   bits.ctypes.data_as(U8), _dp(p), _dp(q0))
+    if bad:
+        raise ValueError("orc_sample rejected its arguments")
+    return bits, p, q0
