@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
-    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100"], default="m144k5",
+    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "disp144"], default="m144k5",
                    help="m100k5: smaller case of the same kernels for profiling; batch256: the 256-instance "
                         "ragged batch; fit100: forward + adjoint of the M=100 kmax=4 fitting loss")
     return p.parse_args()
@@ -333,6 +333,53 @@ def bench_fit(args):
                                  "subsets": N, "params": 2 * M}}), flush=True)
 
 
+def bench_displaced(args):
+    """Displaced-state click-cumulant table, M=144 kmax=5 (the headline instance fed
+    with coherent input displacements, |alpha| ~ 0.5), FP64, beside the zero-mean
+    FP64 table of the same covariance."""
+    import torch
+    import synthetic
+    import paper_2511_14923_gb300 as gbs
+    gbs.build()
+    inst = synthetic.config(2)
+    mean = synthetic.displaced_mean(inst, seed=2025, alpha_scale=0.5)
+    V = torch.from_numpy(inst.V).cuda()
+    m = torch.from_numpy(mean).cuda()
+    N = gbs.table_size(inst.M, inst.kmax)
+    out = torch.empty(N, dtype=torch.float64, device="cuda")
+    ws = gbs.Workspace(inst.M, inst.kmax, "fp64")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    res = {}
+    for name, fn in (("displaced", lambda: gbs.displaced_tables(V, m, 5, "kappa", out=out, workspace=ws, check=False)),
+                     ("zero_mean", lambda: gbs.cumulants(V, 5, "fp64", out=out, workspace=ws, check=False))):
+        for _ in range(args.warmup):
+            fn()
+        if ws.status() != 0:
+            raise SystemExit(f"{name}: device status {ws.status()}")
+        gbs.timing(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        order_ms = np.zeros(6)
+        for s, (a, b) in enumerate(ev):
+            flush.fill_(float(s))
+            a.record()
+            fn()
+            b.record()
+            order_ms += np.array(gbs.timing_read())
+        torch.cuda.synchronize()
+        gbs.timing(False)
+        res[name] = (sum(a.elapsed_time(b) for a, b in ev) / args.steps, (order_ms / args.steps).tolist())
+    ms = res["displaced"][0]
+    print(json.dumps({"metric": "subsets/s, displaced-state click-cumulant table M=144 kmax=5",
+                      "value": N / (ms * 1e-3), "unit": "subsets/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "M=144 kmax=5 instance with coherent input displacements "
+                                             "(alpha ~ 0.5 (N + iN)/sqrt 2, seed 2025)", "subsets": N,
+                                 "l2": "flushed between steps"},
+                      "order_ms": res["displaced"][1],
+                      "zero_mean_fp64": {"ms_per_step": res["zero_mean"][0], "order_ms": res["zero_mean"][1]}}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -340,6 +387,9 @@ def main():
         return
     if args.workload == "batch256":
         bench_batch(args)
+        return
+    if args.workload == "disp144":
+        bench_displaced(args)
         return
     if args.workload == "fit100":
         bench_fit(args)

@@ -168,6 +168,40 @@ typedef enum {
 int gbs_displaced_tables(const double *V, const double *mean, int M, int kmax, int table, double *out,
                          void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- stage 2: sampler */
+
+/* Arithmetic of the sampler's tables and sums. */
+typedef enum {
+    GBS_SAMPLE_FP64 = 0,
+    GBS_SAMPLE_FP32 = 1  /* cumulants converted to FP32 in the workspace, as the paper stores them */
+} gbs_sample_precision;
+
+/* Workspace bytes for gbs_sample with this (M, K, batch, precision); 0 if invalid.
+   Grows as batch x C(M, 3) entries for K = 5 (the p2 table and the stored
+   products), batch x C(M, 2) for K = 3. */
+size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);
+
+/* Chain-rule sampler (Sec. "The sampling algorithm"): draws n_samples threshold-
+   detector bitstrings of M bits from the spin-cumulant table kappa (orders 1..K,
+   gbs.h layout, as gbs_spin_cumulants writes it), bit n from the bias of
+   Eq. delta_bias truncated at order K with approximated marginals:
+     K = 3: single elision (Eq. methprob, Eq. b, Eq. a);
+     K = 5: double elision (Eq. probade, Eq. probpartialade, Eq. probelidedade,
+            Eq. probdoubleelidedade), orders[] = expansion orders of p+, p1, p2
+            (host array, NULL = the paper's 3, 3, 2; each 1..3, 1..3, 1..2).
+   Bit n of a sample is 0 when u[s][n] < q0, q0 = max(p0, 0) / (max(p0, 0) +
+   max(p1, 0)) with p0, p1 the expansion's values for the two outcomes (1/2 if
+   both are <= 0). u: device [n_samples][M] uniforms in [0, 1). force (device,
+   may be NULL): [n_samples][M] bits to score instead of drawing; u is then
+   ignored. Outputs (device): bits_out [n_samples][M]; prob_out [n_samples]
+   (may be NULL) = the estimated probability of each bitstring; q0_out
+   [n_samples][M] (may be NULL). Samples run in chunks of batch (a multiple of
+   64) sharing one workspace of gbs_sampler_workspace_bytes(M, K, batch,
+   precision) bytes. Asynchronous on cuda_stream. */
+int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_samples, const double *u,
+               const uint8_t *force, uint8_t *bits_out, double *prob_out, double *q0_out, int batch, int precision,
+               void *workspace, size_t ws_bytes, void *cuda_stream);
+
 /* ---------------------------------------------------------------- schedule autotuning */
 
 /* Times gbs_cumulants for this (M, kmax, precision) under each candidate

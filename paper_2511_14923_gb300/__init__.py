@@ -82,6 +82,9 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp]
         f.restype = i32
+    L.gbs_sampler_workspace_bytes.argtypes = [i32, i32, i32, i32]; L.gbs_sampler_workspace_bytes.restype = sz
+    L.gbs_sample.argtypes = [vp, i32, i32, ctypes.POINTER(i32), i32, vp, vp, vp, vp, vp, i32, i32, vp, sz, vp]
+    L.gbs_sample.restype = i32
     L.gbs_displaced_tables.argtypes = [vp, vp, i32, i32, i32, vp, vp, sz, vp]
     L.gbs_displaced_tables.restype = i32
     _lib = L
@@ -213,6 +216,53 @@ def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, che
     if check:
         _check(ws.status(st))
     return out
+
+
+SAMPLE_PRECISIONS = {"fp64": 0, "fp32": 1}
+
+
+def sampler_workspace_bytes(M: int, K: int, batch: int, precision: str = "fp32") -> int:
+    return int(lib().gbs_sampler_workspace_bytes(M, K, batch, SAMPLE_PRECISIONS[precision]))
+
+
+def sample(kappa, M: int, K: int, u=None, force=None, orders=None, batch: int = 1024, precision: str = "fp32",
+           want_q0: bool = False, workspace=None, check: bool = True):
+    """Chain-rule sampler (gbs_sample): bitstrings drawn from the spin-cumulant table
+    kappa (CUDA float64, orders 1..K). u: (n, M) CUDA float64 uniforms, or force:
+    (n, M) CUDA uint8 bits to score. Returns (bits (n, M) uint8, prob (n,) float64,
+    q0 (n, M) float64 or None)."""
+    kappa = _dev64(kappa, "kappa")
+    if kappa.numel() != table_size(M, K):
+        raise ValueError(f"kappa must hold table_size(M, K) = {table_size(M, K)} entries")
+    src = force if force is not None else u
+    if src is None:
+        raise ValueError("give u or force")
+    n = src.shape[0]
+    if u is not None:
+        u = _dev64(u, "u")
+        if tuple(u.shape) != (n, M):
+            raise ValueError("u must be (n, M)")
+    if force is not None:
+        if not isinstance(force, torch.Tensor) or not force.is_cuda or force.dtype != torch.uint8:
+            raise TypeError("force must be a CUDA uint8 tensor")
+        force = force.contiguous()
+    dev = kappa.device
+    bits = torch.empty((n, M), dtype=torch.uint8, device=dev)
+    prob = torch.empty(n, dtype=torch.float64, device=dev)
+    q0 = torch.empty((n, M), dtype=torch.float64, device=dev) if want_q0 else None
+    nb = sampler_workspace_bytes(M, K, batch, precision)
+    if nb == 0:
+        raise GbsError(1, f"invalid sampler shape (M={M}, K={K}, batch={batch}, precision={precision})")
+    ws = workspace if workspace is not None else torch.empty(nb, dtype=torch.uint8, device=dev)
+    ordv = None if orders is None else (ctypes.c_int * 3)(*[int(o) for o in orders])
+    st = torch.cuda.current_stream(dev)
+    _check(lib().gbs_sample(_vp(kappa), M, K, ordv, n, None if u is None else _vp(u),
+                            None if force is None else _vp(force), _vp(bits), _vp(prob),
+                            None if q0 is None else _vp(q0), batch, SAMPLE_PRECISIONS[precision], _vp(ws),
+                            ws.numel(), ctypes.c_void_p(st.cuda_stream)))
+    if check:
+        torch.cuda.synchronize(dev)
+    return bits, prob, q0
 
 
 def _vp(t: torch.Tensor):

@@ -1,0 +1,597 @@
+// Stage 2 of the emulator: the chain-rule sampler (arXiv:2511.14923, Sec. "The
+// sampling algorithm", Sec. Methods and App. "Approximating marginals efficiently
+// with a chain rule"), for a batch of S samples drawn in lockstep.
+//
+// The rule. For bits x_1..x_M (bit n = mode n-1), Eq. probs_corr_cumulants_3
+// truncated at order K expands p(x_n..x_1) over the spin cumulants kappa(R+{n}),
+// |R| < K, times marginals p(x_{[n-1]-R}) that are approximated by tables:
+//   P[a] = p(x_a..x_1),  Pp[a][b] = p+(x_a..x_b),  P1[a][e] = p1(x_a..~x_e..x_1),
+//   P2[a][e][d] = p2(x_a..~x_e..~x_d..x_1)  (K = 5 only),
+// filled by truncated forms of the same rule: K = 3 single elision (Eq. methprob,
+// Eq. b, Eq. a), K = 5 double elision (Eq. probade, Eq. probpartialade,
+// Eq. probelidedade, Eq. probdoubleelidedade; orders 3, 3, 2 for p+, p1, p2 unless
+// the caller lowers them). Boundary cases: P[0] = 1, an empty p+ range is 1,
+// P1[a][a] = P[a-1], P2[a][a][d] = P1[a-1][d].
+//
+// Scaling. Each table entry over m variables is stored times 2^m. The factors
+// 1/2, 1/4, ... of the rule then cancel exactly (every term of a sum covers the
+// same number of variables), the stored values stay near 1 instead of 2^-M, and
+// p(x_n = 0) = (P~[n-1] + B~) / 2^n, p(x_n = 1) = (P~[n-1] - B~) / 2^n.
+//
+// Factorisation of the expensive terms. The terms of the bias B that reach back
+// to a table row j - 1 through P2[j-1] (or P1[j-1] for K = 3) are sums over
+// pairs (or single indices) below j of kappa(.., j, i, m) W_j, with
+// W_j(e, d) = chi_e chi_d P2~[j-1][e][d] (K = 3: W_j(d) = chi_d P1~[j-1][d]).
+// W_j only involves bits below j, so right after bit j - 1 is drawn one matrix
+// product per step,
+//   Z_j[row][s] = sum_r kappa[base(row) + r] W_j[r][s],
+// evaluates those sums for every later (i, m) at once; in colex order the
+// kappa entries of one row are contiguous, so each row is a segment of the
+// table. The rows at step j are (K = 5) the order-3 set {., ., j} (used at this
+// step), the order-4 sets {., ., j, n} and the order-5 sets {., ., j, i, m};
+// (K = 3) the order-2 set {., j} and the order-3 sets {., j, n}. At step n the
+// bias then only combines stored Z values with p+ factors:
+//   K = 5: B~ = kappa_n P~[n-1] + sum_i kappa(i,n) chi_i P1~[n-1][i] + G3
+//             + sum_{i<n} chi_i Pp~[n-1][i+1] (Z3_i(n) + sum_{j<i} chi_j Pp~[i-1][j+1] Z5_j(i,n))
+//   K = 3: B~ = kappa_n P~[n-1] + G2 + sum_{i<n} chi_i Pp~[n-1][i+1] Z_i(n)
+// (chi_n taken as +1: every term but P~[n-1] is odd in x_n).
+//
+// Drawing. x_n = 0 when u_n < q0 = max(p0, 0) / (max(p0, 0) + max(p1, 0))
+// (1/2 if both are <= 0); P[n] keeps the chosen branch unclipped.
+//
+// Layout. Every per-sample array is [entry][S] (sample index fastest), so a warp
+// always touches 32 consecutive samples of one entry.
+#include <cstdint>
+#include <cstdio>
+
+#include "gbs.h"
+#include "gbs_common.cuh"
+#include "gbs_sampler.cuh"
+
+namespace gbs {
+namespace smp {
+
+constexpr int BM = 64, BN = 64, BK = 16;  // matrix-product tile (rows x samples x inner)
+
+__host__ __device__ __forceinline__ uint64_t cb(int n, int k) { return binom(n, k); }
+
+// Entry indices (variables 1-based).
+__host__ __device__ __forceinline__ uint64_t i_pp(int a, int b) { return cb(a, 2) + (uint64_t)(b - 1); }       // 1<=b<=a
+__host__ __device__ __forceinline__ uint64_t i_p1(int a, int e) { return cb(a - 1, 2) + (uint64_t)(e - 1); }   // 1<=e<a
+__host__ __device__ __forceinline__ uint64_t i_p2(int a, int e, int d) {                                          // d<e<a
+    return cb(a - 1, 3) + cb(e - 1, 2) + (uint64_t)(d - 1);
+}
+__host__ __device__ __forceinline__ uint64_t i_z(int t, int n) { return cb(n - 1, 2) + (uint64_t)(t - 1); }     // t<n
+__host__ __device__ __forceinline__ uint64_t i_z5(int t, int i, int m) {                                         // t<i<m
+    return cb(m - 1, 3) + cb(i - 1, 2) + (uint64_t)(t - 1);
+}
+
+template <class R>
+struct Args {
+    const R *kap;          // spin cumulants, orders 1..K, gbs.h layout
+    uint64_t off[6];       // order offsets of the cumulant table
+    int M, K, S, opp, op1, op2;
+    R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y;
+    const double *u;       // [n_samples][M] uniforms (chunk base)
+    const uint8_t *force;  // [n_samples][M] or null
+    uint8_t *bits;         // [n_samples][M]
+    double *q0;            // [n_samples][M] or null
+    int n_valid;           // samples of this chunk that are real
+};
+
+template <class R>
+__device__ __forceinline__ R pp(const Args<R> &a, int x, int b, int s) {
+    return b > x ? R(1) : a.Pp[i_pp(x, b) * a.S + s];
+}
+template <class R>
+__device__ __forceinline__ R p1(const Args<R> &a, int x, int e, int s) {
+    return e == x ? a.P[(size_t)(x - 1) * a.S + s] : a.P1[i_p1(x, e) * a.S + s];
+}
+template <class R>
+__device__ __forceinline__ R p2(const Args<R> &a, int x, int e, int d, int s) {
+    return e == x ? p1(a, x - 1, d, s) : a.P2[i_p2(x, e, d) * a.S + s];
+}
+template <class R>
+__device__ __forceinline__ R chi(const Args<R> &a, int v, int s) {
+    return a.chi[(size_t)v * a.S + s];
+}
+// kappa of the sorted variable set (v_1 < .. < v_d), 1-based.
+template <class R>
+__device__ __forceinline__ R k1(const Args<R> &a, int n) { return a.kap[a.off[1] + (n - 1)]; }
+template <class R>
+__device__ __forceinline__ R k2(const Args<R> &a, int i, int n) { return a.kap[a.off[2] + cb(n - 1, 2) + (i - 1)]; }
+template <class R>
+__device__ __forceinline__ R k3(const Args<R> &a, int j, int i, int n) {
+    return a.kap[a.off[3] + cb(n - 1, 3) + cb(i - 1, 2) + (j - 1)];
+}
+
+// (x, y, z) -> decreasing order
+__device__ __forceinline__ void ord3(int x, int y, int z, int &p, int &q, int &r) {
+    if (x < y) { int t = x; x = y; y = t; }
+    if (y < z) { int t = y; y = z; z = t; }
+    if (x < y) { int t = x; x = y; y = t; }
+    p = x; q = y; r = z;
+}
+
+// Pair rank -> (hi, lo), hi > lo >= 0 (colex: rank = C(hi, 2) + lo).
+__device__ __forceinline__ void pair_of(uint64_t r, int &hi, int &lo) {
+    int c = (int)(0.5 * (1.0 + sqrt(1.0 + 8.0 * (double)r)));
+    while (cb(c, 2) > r) --c;
+    while (cb(c + 1, 2) <= r) ++c;
+    hi = c;
+    lo = (int)(r - cb(c, 2));
+}
+
+// ---------------------------------------------------------------- step t: Z rows
+
+// Rows of the product at step t and where each result goes. kbase = offset of the
+// row's segment in the cumulant table; dst = its output entry (or -1 for G).
+__device__ __forceinline__ void zrow(int K, int M, int t, uint64_t q, const uint64_t *off, uint64_t &kbase,
+                                     int &kind, uint64_t &dst) {
+    if (K == 3) {
+        if (q == 0) {
+            kbase = off[2] + cb(t - 1, 2);
+            kind = 0;
+            dst = 0;
+        } else {
+            const int n = t + (int)q;
+            kbase = off[3] + cb(n - 1, 3) + cb(t - 1, 2);
+            kind = 1;
+            dst = i_z(t, n);
+        }
+        return;
+    }
+    if (q == 0) {
+        kbase = off[3] + cb(t - 1, 3);
+        kind = 0;
+        dst = 0;
+    } else if (q <= (uint64_t)(M - t)) {
+        const int n = t + (int)q;
+        kbase = off[4] + cb(n - 1, 4) + cb(t - 1, 3);
+        kind = 1;
+        dst = i_z(t, n);
+    } else {
+        int hi, lo;
+        pair_of(q - 1 - (uint64_t)(M - t), hi, lo);
+        const int i = t + 1 + lo, m = t + 1 + hi;
+        kbase = off[5] + cb(m - 1, 5) + cb(i - 1, 4) + cb(t - 1, 3);
+        kind = 2;
+        dst = i_z5(t, i, m);
+    }
+}
+
+// Z[row][s] = sum_{r < D} kappa[kbase(row) + r] W_t[r][s] for rows [0, rows),
+// samples [0, S). Tiled through shared memory: BM rows x BN samples per CTA,
+// BK inner entries per stage, 4 x 4 results per thread.
+template <class R, int K>
+__global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t rows, int D) {
+    __shared__ R As[BK][BM];
+    __shared__ R Bs[BK][BN];
+    __shared__ uint64_t kb[BM];
+    __shared__ uint64_t dst[BM];
+    __shared__ int kind[BM];
+    __shared__ uint64_t wsrc[BK];   // W source entry (see below)
+    __shared__ int wsel[BK];        // 0: P2/P1 main table, 1: P1/P boundary table
+    __shared__ int we[BK], wd[BK];  // chi indices of W's row
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const uint64_t m0 = (uint64_t)blockIdx.x * BM;
+    const int s0 = blockIdx.y * BN;
+    if (tid < BM) {
+        const uint64_t q = m0 + tid;
+        if (q < rows) zrow(K, a.M, t, q, a.off, kb[tid], kind[tid], dst[tid]);
+        else kind[tid] = -1;
+    }
+    R acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = R(0);
+    for (int k0 = 0; k0 < D; k0 += BK) {
+        if (tid < BK) {
+            const int r = k0 + tid;
+            if (r < D) {
+                if (K == 3) {
+                    // W_t(d) = chi_d P1~[t-1][d], d = r + 1 (d = t - 1 -> P~[t-2])
+                    const int d = r + 1;
+                    we[tid] = d;
+                    wd[tid] = 0;
+                    if (d == t - 1) { wsel[tid] = 1; wsrc[tid] = (uint64_t)(t - 2); }
+                    else { wsel[tid] = 0; wsrc[tid] = i_p1(t - 1, d); }
+                } else {
+                    // W_t(e, d) = chi_e chi_d P2~[t-1][e][d], pair rank r over modes < t - 1
+                    int hi, lo;
+                    pair_of((uint64_t)r, hi, lo);
+                    const int e = hi + 1, d = lo + 1;
+                    we[tid] = e;
+                    wd[tid] = d;
+                    if (e < t - 1) { wsel[tid] = 0; wsrc[tid] = i_p2(t - 1, e, d); }
+                    else if (d < t - 2) { wsel[tid] = 1; wsrc[tid] = i_p1(t - 2, d); }  // P2[t-1][t-1][d] = P1[t-2][d]
+                    else { wsel[tid] = 2; wsrc[tid] = (uint64_t)(t - 3); }              // = P[t-3]
+                }
+            }
+        }
+        __syncthreads();
+        // A: BM x BK from row segments (consecutive threads walk one row's entries)
+        for (int e = tid; e < BM * BK; e += 256) {
+            const int m = e / BK, k = e % BK;
+            R v = R(0);
+            if (kind[m] >= 0 && k0 + k < D) v = a.kap[kb[m] + k0 + k];
+            As[k][m] = v;
+        }
+        // B: BK x BN, W built on the fly from the tables and the spins
+        for (int e = tid; e < BK * BN; e += 256) {
+            const int k = e / BN, s = s0 + (e % BN);
+            R v = R(0);
+            if (k0 + k < D) {
+                const uint64_t src = wsrc[k];
+                if (K == 3) {
+                    v = (wsel[k] == 0 ? a.P1[src * a.S + s] : a.P[src * a.S + s]) * chi(a, we[k], s);
+                } else {
+                    const R tab = wsel[k] == 0 ? a.P2[src * a.S + s]
+                                               : (wsel[k] == 1 ? a.P1[src * a.S + s] : a.P[src * a.S + s]);
+                    v = tab * chi(a, we[k], s) * chi(a, wd[k], s);
+                }
+            }
+            Bs[k][e % BN] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            R av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = ty * 4 + i;
+        if (kind[m] < 0) continue;
+        R *out = kind[m] == 0 ? a.G : (kind[m] == 1 ? a.Z + dst[m] * a.S : a.Z5 + dst[m] * a.S);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[s0 + tx * 4 + j] = acc[i][j];
+    }
+}
+
+// ---------------------------------------------------------------- step n: bias and draw
+
+// K = 5: Y[i][s] = Z3_i(n) + sum_{3 <= j < i} chi_j Pp~[i-1][j+1] Z5_j(i, n), 3 <= i < n.
+template <class R>
+__global__ void y_kernel(Args<R> a, int n) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(g % a.S);
+    const int i = 3 + (int)(g / a.S);
+    if (i >= n) return;
+    R y = a.Z[i_z(i, n) * a.S + s];
+    for (int j = 3; j < i; ++j) y = fma(chi(a, j, s) * pp(a, i - 1, j + 1, s), a.Z5[i_z5(j, i, n) * a.S + s], y);
+    a.Y[(size_t)i * a.S + s] = y;
+}
+
+template <class R, int K>
+__global__ void bias_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    const R Pm = a.P[(size_t)(n - 1) * a.S + s];
+    R B = k1(a, n) * Pm;
+    if (K == 3) {
+        if (n >= 2) B += a.G[s];
+        for (int i = 2; i < n; ++i) B = fma(chi(a, i, s) * pp(a, n - 1, i + 1, s), a.Z[i_z(i, n) * a.S + s], B);
+    } else {
+        for (int i = 1; i < n; ++i) B = fma(k2(a, i, n) * chi(a, i, s), p1(a, n - 1, i, s), B);
+        if (n >= 3) B += a.G[s];
+        for (int i = 3; i < n; ++i) B = fma(chi(a, i, s) * pp(a, n - 1, i + 1, s), a.Y[(size_t)i * a.S + s], B);
+    }
+    const R p0 = Pm + B, p1v = Pm - B;
+    const R c0 = p0 > R(0) ? p0 : R(0), c1 = p1v > R(0) ? p1v : R(0);
+    const R q = (c0 + c1 > R(0)) ? c0 / (c0 + c1) : R(0.5);
+    int x = 0;
+    const bool real = s < a.n_valid;
+    if (real) {
+        const size_t o = (size_t)s * a.M + (n - 1);
+        if (a.force) x = a.force[o] ? 1 : 0;
+        else x = (a.u[o] < (double)q) ? 0 : 1;
+        a.bits[o] = (uint8_t)x;
+        if (a.q0) a.q0[o] = (double)q;
+    }
+    a.chi[(size_t)n * a.S + s] = x ? R(-1) : R(1);
+    a.P[(size_t)n * a.S + s] = x ? p1v : p0;
+}
+
+// ---------------------------------------------------------------- step n: table rows
+
+// Pp~[n][l], l = 1..n (Eq. a / Eq. probpartialade). Thread per (l, sample).
+template <class R>
+__global__ void pp_kernel(Args<R> a, int n) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(g % a.S);
+    const int l = 1 + (int)(g / a.S);
+    if (l > n) return;
+    const R cn = chi(a, n, s);
+    R v = (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s);
+    if (a.opp >= 2)
+        for (int i = l; i < n; ++i)
+            v = fma(k2(a, i, n) * chi(a, i, s) * cn * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), v);
+    if (a.opp >= 3)
+        for (int i = l + 1; i < n; ++i) {
+            const R fi = chi(a, i, s) * cn * pp(a, n - 1, i + 1, s);
+            for (int j = l; j < i; ++j)
+                v = fma(k3(a, j, i, n) * fi * chi(a, j, s) * pp(a, i - 1, j + 1, s), pp(a, j - 1, l, s), v);
+        }
+    a.Pp[i_pp(n, l) * a.S + s] = v;
+}
+
+// P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade). Thread per (e, sample).
+template <class R, int K>
+__global__ void p1_kernel(Args<R> a, int n) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(g % a.S);
+    const int e = 1 + (int)(g / a.S);
+    if (e >= n) return;
+    const R cn = chi(a, n, s);
+    R v = (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s);
+    if (a.op1 >= 2)
+        for (int i = 1; i < n; ++i) {
+            if (i == e) continue;
+            const int hi = i > e ? i : e, lo = i > e ? e : i;
+            const R g2 = k2(a, i, n) * chi(a, i, s) * cn;
+            if (K == 3) v = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), v);
+            else v = fma(g2, p2(a, n - 1, hi, lo, s), v);
+        }
+    if (K == 5 && a.op1 >= 3)
+        for (int i = 2; i < n; ++i) {
+            if (i == e) continue;
+            for (int j = 1; j < i; ++j) {
+                if (j == e) continue;
+                int x, y, z;
+                ord3(i, j, e, x, y, z);
+                v = fma(k3(a, j, i, n) * chi(a, i, s) * chi(a, j, s) * cn * pp(a, n - 1, x + 1, s), p2(a, x - 1, y, z, s),
+                        v);
+            }
+        }
+    a.P1[i_p1(n, e) * a.S + s] = v;
+}
+
+// P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade). Thread per ((e, d), sample).
+template <class R>
+__global__ void p2_kernel(Args<R> a, int n) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(g % a.S);
+    const uint64_t r = g / a.S;
+    if (r >= cb(n - 1, 2)) return;
+    int hi, lo;
+    pair_of(r, hi, lo);
+    const int e = hi + 1, d = lo + 1;
+    const R cn = chi(a, n, s);
+    R v = (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s);
+    if (a.op2 >= 2)
+        for (int i = 1; i < n; ++i) {
+            if (i == e || i == d) continue;
+            int x, y, z;
+            ord3(i, e, d, x, y, z);
+            v = fma(k2(a, i, n) * chi(a, i, s) * cn * pp(a, n - 1, x + 1, s), p2(a, x - 1, y, z, s), v);
+        }
+    a.P2[i_p2(n, e, d) * a.S + s] = v;
+}
+
+template <class R>
+__global__ void init_kernel(Args<R> a) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < a.S) {
+        a.P[s] = R(1);
+        a.chi[s] = R(1);
+    }
+}
+
+template <class R>
+__global__ void prob_kernel(Args<R> a, double *prob) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < a.n_valid) prob[s] = ldexp((double)a.P[(size_t)a.M * a.S + s], -a.M);
+}
+
+__global__ void convert_kernel(const double *__restrict__ in, float *__restrict__ out, uint64_t n) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+// ---------------------------------------------------------------- host side
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+SamplerLayout sampler_layout(int M, int K, int S, int precision) {
+    SamplerLayout L{};
+    const size_t es = precision == 0 ? sizeof(double) : sizeof(float);
+    const size_t Ss = (size_t)S;
+    size_t off = 0;
+    auto take = [&](size_t &field, size_t entries) {
+        field = off;
+        off = a256(off + entries * Ss * es);
+    };
+    take(L.chi, (size_t)M + 1);
+    take(L.P, (size_t)M + 1);
+    take(L.Pp, cb(M, 2) + (size_t)M);
+    take(L.P1, cb(M, 2));
+    take(L.P2, K == 5 ? cb(M, 3) : 0);
+    take(L.Z, cb(M, 2));
+    take(L.Z5, K == 5 ? cb(M, 3) : 0);
+    take(L.G, 1);
+    take(L.Y, K == 5 ? (size_t)M + 1 : 0);
+    L.kap = off;
+    uint64_t nk = 0;
+    for (int d = 1; d <= K; ++d) nk += cb(M, d);
+    if (precision != 0) off = a256(off + nk * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+template <class R, int K>
+static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
+    const int S = a.S, M = a.M;
+    const int TB = 256;
+    init_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a);
+    for (int t = 1; t <= M; ++t) {
+        // products for this step and later ones (inputs: rows < t of the tables)
+        const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);
+        if (D > 0) {
+            const uint64_t rows = K == 3 ? 1 + (uint64_t)(M - t) : 1 + (uint64_t)(M - t) + cb(M - t, 2);
+            dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)(S / BN));
+            zgemm_kernel<R, K><<<grid, 256, 0, st>>>(a, t, rows, D);
+        }
+        if (K == 5 && t > 3) {
+            const uint64_t nt = (uint64_t)(t - 3) * S;
+            y_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
+        }
+        bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
+        {
+            const uint64_t nt = (uint64_t)t * S;
+            pp_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
+        }
+        if (t > 1) {
+            const uint64_t nt = (uint64_t)(t - 1) * S;
+            p1_kernel<R, K><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
+        }
+        if (K == 5 && t > 2) {
+            const uint64_t nt = cb(t - 1, 2) * S;
+            p2_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (prob) prob_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a, prob);
+    return cudaGetLastError();
+}
+
+template <class R>
+static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
+    const SamplerLayout L = sampler_layout(c.M, c.K, c.S, c.precision);
+    char *w = static_cast<char *>(c.ws);
+    Args<R> a{};
+    a.M = c.M;
+    a.K = c.K;
+    a.S = c.S;
+    a.opp = c.K == 3 ? 2 : c.orders[0];
+    a.op1 = c.K == 3 ? 2 : c.orders[1];
+    a.op2 = c.orders[2];
+    a.off[0] = 0;
+    for (int d = 1; d <= 5; ++d) a.off[d] = order_offset(c.M, d);
+    a.chi = reinterpret_cast<R *>(w + L.chi);
+    a.P = reinterpret_cast<R *>(w + L.P);
+    a.Pp = reinterpret_cast<R *>(w + L.Pp);
+    a.P1 = reinterpret_cast<R *>(w + L.P1);
+    a.P2 = reinterpret_cast<R *>(w + L.P2);
+    a.Z = reinterpret_cast<R *>(w + L.Z);
+    a.Z5 = reinterpret_cast<R *>(w + L.Z5);
+    a.G = reinterpret_cast<R *>(w + L.G);
+    a.Y = reinterpret_cast<R *>(w + L.Y);
+    if (sizeof(R) == sizeof(double)) {
+        a.kap = reinterpret_cast<const R *>(c.kappa);
+    } else {
+        uint64_t nk = 0;
+        for (int d = 1; d <= c.K; ++d) nk += cb(c.M, d);
+        float *kf = reinterpret_cast<float *>(w + L.kap);
+        convert_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(c.kappa, kf, nk);
+        a.kap = reinterpret_cast<const R *>(kf);
+    }
+    for (int s0 = 0; s0 < c.n_samples; s0 += c.S) {
+        a.n_valid = c.n_samples - s0 < c.S ? c.n_samples - s0 : c.S;
+        const size_t o = (size_t)s0 * c.M;
+        a.u = c.u ? c.u + o : nullptr;
+        a.force = c.force ? c.force + o : nullptr;
+        a.bits = c.bits + o;
+        a.q0 = c.q0 ? c.q0 + o : nullptr;
+        cudaError_t e = c.K == 3 ? run_chunk<R, 3>(a, c.prob ? c.prob + s0 : nullptr, st)
+                                 : run_chunk<R, 5>(a, c.prob ? c.prob + s0 : nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_sampler(const SamplerCall &c, cudaStream_t st) {
+    return c.precision == 0 ? run_all<double>(c, st) : run_all<float>(c, st);
+}
+
+}  // namespace smp
+}  // namespace gbs
+
+// ---------------------------------------------------------------- C ABI
+
+namespace gbs {
+int record_error(int code, const char *msg);
+}
+
+namespace {
+
+bool dev_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool valid_shape(int M, int K, int batch, int precision) {
+    return (K == 3 || K == 5) && M >= K && M <= GBS_MAX_MODES && batch >= 64 && batch % 64 == 0 &&
+           (precision == GBS_SAMPLE_FP64 || precision == GBS_SAMPLE_FP32);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision) {
+    if (!valid_shape(M, K, batch, precision)) return 0;
+    return gbs::smp::sampler_layout(M, K, batch, precision).total;
+}
+
+int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_samples, const double *u,
+               const uint8_t *force, uint8_t *bits_out, double *prob_out, double *q0_out, int batch, int precision,
+               void *workspace, size_t ws_bytes, void *cuda_stream) {
+    using gbs::record_error;
+    if (!valid_shape(M, K, batch, precision))
+        return record_error(GBS_ERR_INVALID_ARG,
+                            "need K in {3, 5}, K <= M <= 1024, batch a positive multiple of 64 and precision "
+                            "GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
+    if (n_samples < 0) return record_error(GBS_ERR_INVALID_ARG, "n_samples must be >= 0");
+    int ord[3] = {3, 3, 2};
+    if (orders) {
+        for (int i = 0; i < 3; ++i) ord[i] = orders[i];
+        if (ord[0] < 1 || ord[0] > 3 || ord[1] < 1 || ord[1] > 3 || ord[2] < 1 || ord[2] > 2)
+            return record_error(GBS_ERR_INVALID_ARG, "orders must be {1..3, 1..3, 1..2}");
+    }
+    if (!kappa || !bits_out || !workspace || (!u && !force))
+        return record_error(GBS_ERR_INVALID_ARG, "kappa, bits_out, workspace and one of u / force must be non-NULL");
+    if (((uintptr_t)kappa & 7) || (u && ((uintptr_t)u & 7)) || (prob_out && ((uintptr_t)prob_out & 7)) ||
+        (q0_out && ((uintptr_t)q0_out & 7)) || ((uintptr_t)workspace & 255))
+        return record_error(GBS_ERR_INVALID_ARG, "double arrays must be 8-byte aligned, the workspace 256-byte aligned");
+    if (!dev_ptr(kappa) || !dev_ptr(bits_out) || !dev_ptr(workspace) || (u && !dev_ptr(u)) ||
+        (force && !dev_ptr(force)) || (prob_out && !dev_ptr(prob_out)) || (q0_out && !dev_ptr(q0_out)))
+        return record_error(GBS_ERR_INVALID_ARG, "all arrays must be CUDA device (or managed) memory");
+    const gbs::smp::SamplerLayout L = gbs::smp::sampler_layout(M, K, batch, precision);
+    if (ws_bytes < L.total) return record_error(GBS_ERR_WORKSPACE, "workspace smaller than gbs_sampler_workspace_bytes()");
+    if (n_samples == 0) return record_error(GBS_OK, "");
+    gbs::smp::SamplerCall c{};
+    c.kappa = kappa;
+    c.M = M;
+    c.K = K;
+    c.S = batch;
+    c.precision = precision;
+    c.n_samples = n_samples;
+    for (int i = 0; i < 3; ++i) c.orders[i] = ord[i];
+    c.u = u;
+    c.force = force;
+    c.bits = bits_out;
+    c.prob = prob_out;
+    c.q0 = q0_out;
+    c.ws = workspace;
+    cudaError_t e = gbs::smp::launch_sampler(c, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return record_error(GBS_ERR_CUDA, cudaGetErrorString(e));
+    return record_error(GBS_OK, "");
+}
+
+}  // extern "C"

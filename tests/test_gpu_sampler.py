@@ -1,0 +1,108 @@
+"""Chain-rule sampler on the GPU (gbs_sample) against the oracle (oracle/sampler.c),
+on the same seeded uniforms.
+
+FP64: the kernels sum in another order than the oracle, so probabilities agree
+to rounding (relative 1e-11 here) and every drawn bit is the oracle's (a
+decision could only differ when u falls within ~1e-13 of q0). FP32 (the
+precision the paper stores its tables in): each GPU decision is checked against
+the oracle's q0 for the GPU's own bitstring (scored with forced bits) -- a bit
+may differ from u < q0 only when |u - q0| < 2e-4 -- and the GPU's q0 and
+probability agree with the oracle's within 2e-4 absolute and 1e-3 relative,
+a bound from the FP32 unit roundoff (6e-8) times the few thousand terms of the
+longest sums at these sizes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+import paper_2511_14923_gb300 as gbs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    gbs.build()
+
+
+def kappa_of(inst, K):
+    return gbs.spin_cumulants(torch.from_numpy(inst.V).cuda(), K, "fp64")
+
+
+def uniforms(n, M, seed):
+    return np.random.default_rng(seed).random((n, M))
+
+
+@pytest.mark.parametrize("K,M,orders,n,batch", [(3, 12, None, 200, 64), (5, 14, None, 200, 128),
+                                                (5, 13, (2, 2, 1), 130, 64), (5, 9, (3, 2, 1), 64, 64),
+                                                (3, 3, None, 64, 64), (5, 5, None, 64, 64)])
+def test_fp64_draws_match_oracle(K, M, orders, n, batch):
+    inst = synthetic.random_instance(M, K, seed=500 + M + K, r_range=(0.5, 1.3))
+    kap = kappa_of(inst, K)
+    u = uniforms(n, M, seed=M * 7 + K)
+    bits, prob, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), orders=orders, batch=batch,
+                                precision="fp64", want_q0=True)
+    rb, rp, rq = oracle.sample(kap.cpu().numpy(), M, K, u=u, orders=orders)
+    assert np.array_equal(bits.cpu().numpy(), rb)
+    np.testing.assert_allclose(prob.cpu().numpy(), rp, rtol=1e-11)
+    assert np.abs(q0.cpu().numpy() - rq).max() <= 1e-12
+
+
+@pytest.mark.parametrize("K", [3, 5])
+def test_fp64_scores_all_bitstrings(K):
+    M = 9
+    inst = synthetic.random_instance(M, K, seed=90 + K)
+    kap = kappa_of(inst, K)
+    allb = ((np.arange(1 << M)[:, None] >> np.arange(M)) & 1).astype(np.uint8)
+    _, prob, _ = gbs.sample(kap, M, K, force=torch.from_numpy(allb).cuda(), batch=128, precision="fp64")
+    _, rp, _ = oracle.sample(kap.cpu().numpy(), M, K, force=allb)
+    p = prob.cpu().numpy()
+    np.testing.assert_allclose(p, rp, rtol=1e-11, atol=1e-17)
+    assert abs(p.sum() - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("K,M", [(3, 24), (5, 20)])
+def test_fp32_decisions_consistent_with_oracle(K, M):
+    inst = synthetic.random_instance(M, K, seed=3200 + M, r_range=(0.6, 1.4), eta_range=(0.3, 0.5))
+    kap = kappa_of(inst, K)
+    n = 256
+    u = uniforms(n, M, seed=11)
+    bits, prob, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+                                want_q0=True)
+    b = bits.cpu().numpy()
+    _, rp, rq = oracle.sample(kap.cpu().numpy(), M, K, force=b)
+    tau = 2e-4
+    assert np.abs(q0.cpu().numpy() - rq).max() <= tau
+    np.testing.assert_allclose(prob.cpu().numpy(), rp, rtol=1e-3)
+    drawn_zero = b == 0
+    assert np.all(np.where(drawn_zero, u < rq + tau, u >= rq - tau))
+
+
+def test_fp32_m144_k5_consistent_on_a_few_samples():
+    """The benchmark's M = 144 state: a handful of FP32 samples scored by the oracle."""
+    inst = synthetic.config(2)
+    kap = kappa_of(inst, 5)
+    n = 64
+    u = uniforms(n, 144, seed=144)
+    bits, prob, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=64, precision="fp32",
+                                want_q0=True)
+    assert bool(torch.isfinite(prob).all()) and bool((prob > 0).all())
+    b = bits.cpu().numpy()[:2]
+    _, rp, rq = oracle.sample(kap.cpu().numpy(), 144, 5, force=b)
+    tau = 2e-4
+    assert np.abs(q0.cpu().numpy()[:2] - rq).max() <= tau
+    np.testing.assert_allclose(prob.cpu().numpy()[:2], rp, rtol=1e-3)
+    assert np.all(np.where(b == 0, u[:2] < rq + tau, u[:2] >= rq - tau))
+
+
+def test_invalid_arguments():
+    inst = synthetic.random_instance(8, 5, seed=1)
+    kap = kappa_of(inst, 5)
+    u = torch.rand(4, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(gbs.GbsError):
+        gbs.sample(kap, 8, 5, u=u, batch=48)
+    with pytest.raises(gbs.GbsError):
+        gbs.sample(kap, 8, 5, u=u, orders=(4, 3, 2))
+    assert gbs.sampler_workspace_bytes(8, 4, 64) == 0
+    assert gbs.sampler_workspace_bytes(4, 5, 64) == 0
