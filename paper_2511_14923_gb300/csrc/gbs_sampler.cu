@@ -28,7 +28,9 @@
 // evaluates those sums for every later (i, m) at once; in colex order the
 // kappa entries of one row are contiguous, so each row is a segment of the
 // table. The rows at step j are (K = 5) the order-3 set {., ., j} (used at this
-// step), the order-4 sets {., ., j, n} and the order-5 sets {., ., j, i, m};
+// step), the order-4 sets {., ., j, n}, the order-5 sets {., ., j, i, m} and the
+// pairs below j of the order-3 sets {., ., n} (X_j(n), the part of the p1 update
+// whose largest index is the elided one);
 // (K = 3) the order-2 set {., j} and the order-3 sets {., j, n}. At step n the
 // bias then only combines stored Z values with p+ factors:
 //   K = 5: B~ = kappa_n P~[n-1] + sum_i kappa(i,n) chi_i P1~[n-1][i] + G3
@@ -71,7 +73,8 @@ struct Args {
     const R *kap;          // spin cumulants, orders 1..K, gbs.h layout
     uint64_t off[6];       // order offsets of the cumulant table
     int M, K, S, opp, op1, op2;
-    R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y;
+    R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X;
+    uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
     uint8_t *bits;         // [n_samples][M]
@@ -95,6 +98,23 @@ template <class R>
 __device__ __forceinline__ R chi(const Args<R> &a, int v, int s) {
     return a.chi[(size_t)v * a.S + s];
 }
+// Spins of one sample read from its packed bits; the current 32-bit word is
+// cached, so a loop over ascending variables loads one word per 32 of them.
+template <class R>
+struct Spins {
+    const uint32_t *bw;
+    int S, s, w;
+    uint32_t cur;
+    __device__ Spins(const Args<R> &a, int s_) : bw(a.bw), S(a.S), s(s_), w(-1), cur(0) {}
+    __device__ __forceinline__ R operator()(int v) {
+        if ((v >> 5) != w) {
+            w = v >> 5;
+            cur = bw[(size_t)w * S + s];
+        }
+        return (cur >> (v & 31)) & 1u ? R(-1) : R(1);
+    }
+};
+
 // kappa of the sorted variable set (v_1 < .. < v_d), 1-based.
 template <class R>
 __device__ __forceinline__ R k1(const Args<R> &a, int n) { return a.kap[a.off[1] + (n - 1)]; }
@@ -150,9 +170,15 @@ __device__ __forceinline__ void zrow(int K, int M, int t, uint64_t q, const uint
         kbase = off[4] + cb(n - 1, 4) + cb(t - 1, 3);
         kind = 1;
         dst = i_z(t, n);
+    } else if (q <= 2 * (uint64_t)(M - t)) {
+        // the pairs below t of the order-3 set {., ., n}: X_t(n) for the p1 update
+        const int n = t + (int)(q - (uint64_t)(M - t));
+        kbase = off[3] + cb(n - 1, 3);
+        kind = 3;
+        dst = i_z(t, n);
     } else {
         int hi, lo;
-        pair_of(q - 1 - (uint64_t)(M - t), hi, lo);
+        pair_of(q - 1 - 2 * (uint64_t)(M - t), hi, lo);
         const int i = t + 1 + lo, m = t + 1 + hi;
         kbase = off[5] + cb(m - 1, 5) + cb(i - 1, 4) + cb(t - 1, 3);
         kind = 2;
@@ -253,7 +279,10 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t r
     for (int i = 0; i < 4; ++i) {
         const int m = ty * 4 + i;
         if (kind[m] < 0) continue;
-        R *out = kind[m] == 0 ? a.G : (kind[m] == 1 ? a.Z + dst[m] * a.S : a.Z5 + dst[m] * a.S);
+        R *out = kind[m] == 0 ? a.G
+               : kind[m] == 1 ? a.Z + dst[m] * a.S
+               : kind[m] == 2 ? a.Z5 + dst[m] * a.S
+                              : a.X + dst[m] * a.S;
 #pragma unroll
         for (int j = 0; j < 4; ++j) out[s0 + tx * 4 + j] = acc[i][j];
     }
@@ -300,10 +329,28 @@ __global__ void bias_kernel(Args<R> a, int n) {
         if (a.q0) a.q0[o] = (double)q;
     }
     a.chi[(size_t)n * a.S + s] = x ? R(-1) : R(1);
+    if (x) a.bw[(size_t)(n >> 5) * a.S + s] |= 1u << (n & 31);
     a.P[(size_t)n * a.S + s] = x ? p1v : p0;
 }
 
 // ---------------------------------------------------------------- step n: table rows
+
+// Order-3 part of the p+ update, factored: the term
+//   sum_{i > j >= l} kappa(j,i,n) chi_i chi_j chi_n Pp~[n-1][i+1] Pp~[i-1][j+1] Pp~[j-1][l]
+// equals chi_n sum_{j >= l} Pp~[j-1][l] v(j) with
+//   v(j) = chi_j sum_{i > j} kappa(j,i,n) chi_i Pp~[n-1][i+1] Pp~[i-1][j+1],
+// which does not depend on l. Thread per (j, sample); v goes to Y (free after the bias).
+template <class R>
+__global__ void pv_kernel(Args<R> a, int n) {
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)(g % a.S);
+    const int j = 1 + (int)(g / a.S);
+    if (j >= n) return;
+    Spins<R> sp(a, s);
+    R v = R(0);
+    for (int i = j + 1; i < n; ++i) v = fma(k3(a, j, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, j + 1, s), v);
+    a.Y[(size_t)j * a.S + s] = v * sp(j);
+}
 
 // Pp~[n][l], l = 1..n (Eq. a / Eq. probpartialade). Thread per (l, sample).
 template <class R>
@@ -312,52 +359,54 @@ __global__ void pp_kernel(Args<R> a, int n) {
     const int s = (int)(g % a.S);
     const int l = 1 + (int)(g / a.S);
     if (l > n) return;
-    const R cn = chi(a, n, s);
-    R v = (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s);
+    Spins<R> sp(a, s);
+    const R cn = sp(n);
+    R acc = R(0);
     if (a.opp >= 2)
-        for (int i = l; i < n; ++i)
-            v = fma(k2(a, i, n) * chi(a, i, s) * cn * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), v);
+        for (int i = l; i < n; ++i) acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), acc);
     if (a.opp >= 3)
-        for (int i = l + 1; i < n; ++i) {
-            const R fi = chi(a, i, s) * cn * pp(a, n - 1, i + 1, s);
-            for (int j = l; j < i; ++j)
-                v = fma(k3(a, j, i, n) * fi * chi(a, j, s) * pp(a, i - 1, j + 1, s), pp(a, j - 1, l, s), v);
-        }
-    a.Pp[i_pp(n, l) * a.S + s] = v;
+        for (int j = l; j < n - 1; ++j) acc = fma(a.Y[(size_t)j * a.S + s], pp(a, j - 1, l, s), acc);
+    a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s));
 }
 
 // P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade). Thread per (e, sample).
+// K = 5, order 3: with (a, b, c) the decreasing order of (i, j, e), the terms with
+// a = e come from the product rows (X_e(n), times Pp~[n-1][e+1]); the others
+// (a = i > e) are summed here over i, each with the factor chi_i Pp~[n-1][i+1].
 template <class R, int K>
 __global__ void p1_kernel(Args<R> a, int n) {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int s = (int)(g % a.S);
     const int e = 1 + (int)(g / a.S);
     if (e >= n) return;
-    const R cn = chi(a, n, s);
-    R v = (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s);
+    Spins<R> sp(a, s);
+    const R cn = sp(n);
+    R acc = R(0);
     if (a.op1 >= 2)
         for (int i = 1; i < n; ++i) {
             if (i == e) continue;
             const int hi = i > e ? i : e, lo = i > e ? e : i;
-            const R g2 = k2(a, i, n) * chi(a, i, s) * cn;
-            if (K == 3) v = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), v);
-            else v = fma(g2, p2(a, n - 1, hi, lo, s), v);
+            const R g2 = k2(a, i, n) * sp(i);
+            if (K == 3) acc = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), acc);
+            else acc = fma(g2, p2(a, n - 1, hi, lo, s), acc);
         }
-    if (K == 5 && a.op1 >= 3)
-        for (int i = 2; i < n; ++i) {
-            if (i == e) continue;
-            for (int j = 1; j < i; ++j) {
-                if (j == e) continue;
-                int x, y, z;
-                ord3(i, j, e, x, y, z);
-                v = fma(k3(a, j, i, n) * chi(a, i, s) * chi(a, j, s) * cn * pp(a, n - 1, x + 1, s), p2(a, x - 1, y, z, s),
-                        v);
-            }
+    if (K == 5 && a.op1 >= 3) {
+        if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * a.S + s], acc);
+        for (int i = e + 1; i < n; ++i) {
+            R t = R(0);
+            // j < e: P2~[i-1][e][j]; j > e: P2~[i-1][j][e]
+            Spins<R> sj(a, s);
+            for (int j = 1; j < e; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, e, j, s), t);
+            for (int j = e + 1; j < i; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, j, e, s), t);
+            acc = fma(sp(i) * pp(a, n - 1, i + 1, s), t, acc);
         }
-    a.P1[i_p1(n, e) * a.S + s] = v;
+    }
+    a.P1[i_p1(n, e) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
 }
 
 // P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade). Thread per ((e, d), sample).
+// Order 2: i > e reaches P2~[i-1][e][d] (factor Pp~[n-1][i+1]); i < e reaches
+// P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]).
 template <class R>
 __global__ void p2_kernel(Args<R> a, int n) {
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,16 +416,17 @@ __global__ void p2_kernel(Args<R> a, int n) {
     int hi, lo;
     pair_of(r, hi, lo);
     const int e = hi + 1, d = lo + 1;
-    const R cn = chi(a, n, s);
-    R v = (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s);
-    if (a.op2 >= 2)
-        for (int i = 1; i < n; ++i) {
-            if (i == e || i == d) continue;
-            int x, y, z;
-            ord3(i, e, d, x, y, z);
-            v = fma(k2(a, i, n) * chi(a, i, s) * cn * pp(a, n - 1, x + 1, s), p2(a, x - 1, y, z, s), v);
-        }
-    a.P2[i_p2(n, e, d) * a.S + s] = v;
+    Spins<R> sp(a, s);
+    const R cn = sp(n);
+    R acc = R(0);
+    if (a.op2 >= 2) {
+        R t = R(0);
+        for (int i = 1; i < d; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, d, i, s), t);
+        for (int i = d + 1; i < e; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, i, d, s), t);
+        acc = pp(a, n - 1, e + 1, s) * t;
+        for (int i = e + 1; i < n; ++i) acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), p2(a, i - 1, e, d, s), acc);
+    }
+    a.P2[i_p2(n, e, d) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
 }
 
 template <class R>
@@ -385,6 +435,7 @@ __global__ void init_kernel(Args<R> a) {
     if (s < a.S) {
         a.P[s] = R(1);
         a.chi[s] = R(1);
+        for (int w = 0; w <= a.M / 32; ++w) a.bw[(size_t)w * a.S + s] = 0u;
     }
 }
 
@@ -421,6 +472,9 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.Z5, K == 5 ? cb(M, 3) : 0);
     take(L.G, 1);
     take(L.Y, K == 5 ? (size_t)M + 1 : 0);
+    take(L.X, K == 5 ? cb(M, 2) : 0);
+    L.bw = off;
+    off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
     L.kap = off;
     uint64_t nk = 0;
     for (int d = 1; d <= K; ++d) nk += cb(M, d);
@@ -438,7 +492,7 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         // products for this step and later ones (inputs: rows < t of the tables)
         const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);
         if (D > 0) {
-            const uint64_t rows = K == 3 ? 1 + (uint64_t)(M - t) : 1 + (uint64_t)(M - t) + cb(M - t, 2);
+            const uint64_t rows = K == 3 ? 1 + (uint64_t)(M - t) : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
             dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)(S / BN));
             zgemm_kernel<R, K><<<grid, 256, 0, st>>>(a, t, rows, D);
         }
@@ -447,6 +501,10 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
             y_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
         }
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
+        if (K == 5 && a.opp >= 3 && t > 1) {
+            const uint64_t nt = (uint64_t)(t - 1) * S;
+            pv_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
+        }
         {
             const uint64_t nt = (uint64_t)t * S;
             pp_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
@@ -488,6 +546,8 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.Z5 = reinterpret_cast<R *>(w + L.Z5);
     a.G = reinterpret_cast<R *>(w + L.G);
     a.Y = reinterpret_cast<R *>(w + L.Y);
+    a.X = reinterpret_cast<R *>(w + L.X);
+    a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
     if (sizeof(R) == sizeof(double)) {
         a.kap = reinterpret_cast<const R *>(c.kappa);
     } else {
