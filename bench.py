@@ -62,8 +62,10 @@ def parse():
                    help="skip gbs_autotune (untimed) before measuring; use the default schedule")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--batch", type=int, default=8192, help="samples per step (sample144)")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
-    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "disp144"], default="m144k5",
+    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "disp144", "sample144"],
+                   default="m144k5",
                    help="m100k5: smaller case of the same kernels for profiling; batch256: the 256-instance "
                         "ragged batch; fit100: forward + adjoint of the M=100 kmax=4 fitting loss")
     return p.parse_args()
@@ -380,6 +382,77 @@ def bench_displaced(args):
           flush=True)
 
 
+PAPER_SAMPLES_PER_GPU_S = 1e7 / (115 * 60) / 8  # 10^7 samples in 115 min on 8 H100 (K = 5, M = 144)
+
+
+def bench_sampler(args):
+    """Stage 2: K = 5 double-elision samples of the M=144 workload's spin-cumulant
+    table (FP32 tables, as the paper stores them), one gbs_sample call of --batch
+    samples per step; uniforms seeded and resident on the device. The FP64 form is
+    timed beside it on a smaller batch."""
+    import torch
+    import synthetic
+    import paper_2511_14923_gb300 as gbs
+    gbs.build()
+    M, K, B = 144, 5, args.batch
+    inst = synthetic.config(2)
+    kap = gbs.spin_cumulants(torch.from_numpy(inst.V).cuda(), K, "fp64")
+    g = torch.Generator(device="cuda").manual_seed(20251114)
+    steps, warm = args.steps, max(args.warmup, 3)
+    us = [torch.rand(B, M, dtype=torch.float64, device="cuda", generator=g) for _ in range(steps + warm)]
+    ws = torch.empty(gbs.sampler_workspace_bytes(M, K, B, "fp32"), dtype=torch.uint8, device="cuda")
+    for w in range(warm):
+        gbs.sample(kap, M, K, u=us[w], batch=B, precision="fp32", workspace=ws, check=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler() as clk:
+        for k, (a, b) in enumerate(ev):
+            a.record()
+            bits, prob, _ = gbs.sample(kap, M, K, u=us[warm + k], batch=B, precision="fp32", workspace=ws,
+                                       check=False)
+            b.record()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    ok = bool(torch.isfinite(prob).all())
+    # end to end: uniforms from pinned host memory in, bitstrings out, every step
+    uh = us[0].cpu().pin_memory()
+    bh = torch.empty((B, M), dtype=torch.uint8).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ud = torch.empty_like(us[0])
+    e0.record()
+    for _ in range(steps):
+        ud.copy_(uh, non_blocking=True)
+        bits, _, _ = gbs.sample(kap, M, K, u=ud, batch=B, precision="fp32", workspace=ws, check=False)
+        bh.copy_(bits, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / steps
+    # FP64 tables on a smaller batch
+    B64 = 512
+    ws64 = torch.empty(gbs.sampler_workspace_bytes(M, K, B64, "fp64"), dtype=torch.uint8, device="cuda")
+    gbs.sample(kap, M, K, u=us[0][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64)
+    e0.record()
+    gbs.sample(kap, M, K, u=us[1][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    value = B / (ms * 1e-3)
+    print(json.dumps({
+        "metric": "samples/s, K=5 double-elision chain-rule sampler, M=144", "value": value, "unit": "samples/s",
+        "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "spin cumulants of the M=144 kmax=5 workload (72 squeezers, per-mode eta), "
+                               "K=5 double elision, orders (3, 3, 2), FP32 tables", "samples_per_step": B,
+                   "inputs": f"{B} x {M} seeded uniforms per step, resident on the device",
+                   "workspace_GB": ws.numel() / 1e9, "l2": "per-step working set (tables of 8192 samples) >> L2"},
+        "paper_context": {"samples_per_s_per_gpu": PAPER_SAMPLES_PER_GPU_S,
+                          "hardware": "8x H100 SXM, 1e7 samples in 115 min", "ratio": value / PAPER_SAMPLES_PER_GPU_S},
+        "fp64_tables": {"samples_per_step": B64, "ms_per_step": ms64, "value": B64 / (ms64 * 1e-3)},
+        "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": B * M * 8,
+                "d2h_bytes_per_step": B * M},
+        "all_finite": ok, "clocks": clk.summary()}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -387,6 +460,9 @@ def main():
         return
     if args.workload == "batch256":
         bench_batch(args)
+        return
+    if args.workload == "sample144":
+        bench_sampler(args)
         return
     if args.workload == "disp144":
         bench_displaced(args)
