@@ -196,7 +196,7 @@ size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);
    ignored. Outputs (device): bits_out [n_samples][M]; prob_out [n_samples]
    (may be NULL) = the estimated probability of each bitstring; q0_out
    [n_samples][M] (may be NULL). Samples run in chunks of batch (a multiple of
-   64) sharing one workspace of gbs_sampler_workspace_bytes(M, K, batch,
+   128) sharing one workspace of gbs_sampler_workspace_bytes(M, K, batch,
    precision) bytes. Asynchronous on cuda_stream. */
 int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_samples, const double *u,
                const uint8_t *force, uint8_t *bits_out, double *prob_out, double *q0_out, int batch, int precision,

@@ -53,7 +53,6 @@
 namespace gbs {
 namespace smp {
 
-constexpr int BM = 64, BN = 64, BK = 16;  // matrix-product tile (rows x samples x inner)
 
 __host__ __device__ __forceinline__ uint64_t cb(int n, int k) { return binom(n, k); }
 
@@ -73,7 +72,7 @@ struct Args {
     const R *kap;          // spin cumulants, orders 1..K, gbs.h layout
     uint64_t off[6];       // order offsets of the cumulant table
     int M, K, S, opp, op1, op2;
-    R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X;
+    R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X, *W;
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -186,105 +185,113 @@ __device__ __forceinline__ void zrow(int K, int M, int t, uint64_t q, const uint
     }
 }
 
-// Z[row][s] = sum_{r < D} kappa[kbase(row) + r] W_t[r][s] for rows [0, rows),
-// samples [0, S). Tiled through shared memory: BM rows x BN samples per CTA,
-// BK inner entries per stage, 4 x 4 results per thread.
+// W_t[r][s], the inner operand of the step-t product: K = 5, pair r = (e, d) of
+// bits below t, chi_e chi_d P2~[t-1][e][d]; K = 3, d = r + 1, chi_d P1~[t-1][d].
+// Grid: (samples / ETB, entries); the entry index is uniform in a block.
+constexpr int ETB = 64;  // threads per block of the per-(entry, sample) kernels
+
 template <class R, int K>
+__global__ void __launch_bounds__(ETB) w_kernel(Args<R> a, int t, int D) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int r = blockIdx.y; r < D; r += gridDim.y) {
+        R v;
+        if (K == 3) {
+            const int d = r + 1;
+            v = p1(a, t - 1, d, s) * chi(a, d, s);
+        } else {
+            int hi, lo;
+            pair_of((uint64_t)r, hi, lo);
+            v = p2(a, t - 1, hi + 1, lo + 1, s) * chi(a, hi + 1, s) * chi(a, lo + 1, s);
+        }
+        a.W[(size_t)r * a.S + s] = v;
+    }
+}
+
+// Z[row][s] = sum_{r < D} kappa[kbase(row) + r] W_t[r][s] for rows [0, rows) and
+// all samples. 256 threads, (16 TM) x (16 TN) results per CTA, TM x TN per
+// thread (two 4-wide halves each way when 8), 8 inner entries per stage with
+// the next stage prefetched into registers.
+template <class R, int K, int TM, int TN>
 __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t rows, int D) {
-    __shared__ R As[BK][BM];
-    __shared__ R Bs[BK][BN];
-    __shared__ uint64_t kb[BM];
-    __shared__ uint64_t dst[BM];
-    __shared__ int kind[BM];
-    __shared__ uint64_t wsrc[BK];   // W source entry (see below)
-    __shared__ int wsel[BK];        // 0: P2/P1 main table, 1: P1/P boundary table
-    __shared__ int we[BK], wd[BK];  // chi indices of W's row
+    constexpr int BMt = 16 * TM, BNt = 16 * TN, BKt = 8;
+    constexpr int AE = BMt * BKt / 256, BE = BNt * BKt / 256;  // elements per thread per stage
+    __shared__ __align__(16) R As[2][BKt][BMt];
+    __shared__ __align__(16) R Bs[2][BKt][BNt];
+    __shared__ uint64_t kb[BMt];
+    __shared__ uint64_t dst[BMt];
+    __shared__ int kind[BMt];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const uint64_t m0 = (uint64_t)blockIdx.x * BM;
-    const int s0 = blockIdx.y * BN;
-    if (tid < BM) {
-        const uint64_t q = m0 + tid;
-        if (q < rows) zrow(K, a.M, t, q, a.off, kb[tid], kind[tid], dst[tid]);
-        else kind[tid] = -1;
+    const uint64_t m0 = (uint64_t)blockIdx.x * BMt;
+    const int s0 = blockIdx.y * BNt;
+    for (int m = tid; m < BMt; m += 256) {
+        const uint64_t q = m0 + m;
+        if (q < rows) zrow(K, a.M, t, q, a.off, kb[m], kind[m], dst[m]);
+        else kind[m] = -1;
     }
-    R acc[4][4];
+    __syncthreads();
+    // stage loaders: A element e = tid + 256 q -> (row e / 8, inner e % 8);
+    // B: BE consecutive samples of inner row tid / (BNt / BE)
+    const int bk = tid / (BNt / BE), bs = (tid % (BNt / BE)) * BE;
+    R ra[AE], rb[BE];
+    auto load = [&](int k0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = R(0);
-    for (int k0 = 0; k0 < D; k0 += BK) {
-        if (tid < BK) {
-            const int r = k0 + tid;
-            if (r < D) {
-                if (K == 3) {
-                    // W_t(d) = chi_d P1~[t-1][d], d = r + 1 (d = t - 1 -> P~[t-2])
-                    const int d = r + 1;
-                    we[tid] = d;
-                    wd[tid] = 0;
-                    if (d == t - 1) { wsel[tid] = 1; wsrc[tid] = (uint64_t)(t - 2); }
-                    else { wsel[tid] = 0; wsrc[tid] = i_p1(t - 1, d); }
-                } else {
-                    // W_t(e, d) = chi_e chi_d P2~[t-1][e][d], pair rank r over modes < t - 1
-                    int hi, lo;
-                    pair_of((uint64_t)r, hi, lo);
-                    const int e = hi + 1, d = lo + 1;
-                    we[tid] = e;
-                    wd[tid] = d;
-                    if (e < t - 1) { wsel[tid] = 0; wsrc[tid] = i_p2(t - 1, e, d); }
-                    else if (d < t - 2) { wsel[tid] = 1; wsrc[tid] = i_p1(t - 2, d); }  // P2[t-1][t-1][d] = P1[t-2][d]
-                    else { wsel[tid] = 2; wsrc[tid] = (uint64_t)(t - 3); }              // = P[t-3]
-                }
-            }
+        for (int q = 0; q < AE; ++q) {
+            const int e = tid + 256 * q, m = e / BKt, k = e % BKt;
+            ra[q] = (kind[m] >= 0 && k0 + k < D) ? a.kap[kb[m] + k0 + k] : R(0);
         }
-        __syncthreads();
-        // A: BM x BK from row segments (consecutive threads walk one row's entries)
-        for (int e = tid; e < BM * BK; e += 256) {
-            const int m = e / BK, k = e % BK;
-            R v = R(0);
-            if (kind[m] >= 0 && k0 + k < D) v = a.kap[kb[m] + k0 + k];
-            As[k][m] = v;
+        const R *w = a.W + (size_t)(k0 + bk) * a.S + s0 + bs;
+#pragma unroll
+        for (int q = 0; q < BE; ++q) rb[q] = (k0 + bk < D) ? w[q] : R(0);
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < AE; ++q) {
+            const int e = tid + 256 * q;
+            As[buf][e % BKt][e / BKt] = ra[q];
         }
-        // B: BK x BN, W built on the fly from the tables and the spins
-        for (int e = tid; e < BK * BN; e += 256) {
-            const int k = e / BN, s = s0 + (e % BN);
-            R v = R(0);
-            if (k0 + k < D) {
-                const uint64_t src = wsrc[k];
-                if (K == 3) {
-                    v = (wsel[k] == 0 ? a.P1[src * a.S + s] : a.P[src * a.S + s]) * chi(a, we[k], s);
-                } else {
-                    const R tab = wsel[k] == 0 ? a.P2[src * a.S + s]
-                                               : (wsel[k] == 1 ? a.P1[src * a.S + s] : a.P[src * a.S + s]);
-                    v = tab * chi(a, we[k], s) * chi(a, wd[k], s);
-                }
-            }
-            Bs[k][e % BN] = v;
+#pragma unroll
+        for (int q = 0; q < BE; ++q) Bs[buf][bk][bs + q] = rb[q];
+    };
+    R acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = R(0);
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < D; k0 += BKt) {
+        const bool more = k0 + BKt < D;
+        if (more) load(k0 + BKt);
+#pragma unroll
+        for (int k = 0; k < BKt; ++k) {
+            R av[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = As[buf][k][(i < 4 ? 0 : BMt / 2) + ty * 4 + (i & 3)];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[buf][k][(j < 4 ? 0 : BNt / 2) + tx * 4 + (j & 3)];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < BK; ++k) {
-            R av[4], bv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[k][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        if (more) {
+            store(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
         }
-        __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = ty * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+        const int m = (i < 4 ? 0 : BMt / 2) + ty * 4 + (i & 3);
         if (kind[m] < 0) continue;
         R *out = kind[m] == 0 ? a.G
                : kind[m] == 1 ? a.Z + dst[m] * a.S
                : kind[m] == 2 ? a.Z5 + dst[m] * a.S
                               : a.X + dst[m] * a.S;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out[s0 + tx * 4 + j] = acc[i][j];
+        for (int j = 0; j < TN; ++j) out[s0 + (j < 4 ? 0 : BNt / 2) + tx * 4 + (j & 3)] = acc[i][j];
     }
 }
 
@@ -292,29 +299,30 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t r
 
 // K = 5: Y[i][s] = Z3_i(n) + sum_{3 <= j < i} chi_j Pp~[i-1][j+1] Z5_j(i, n), 3 <= i < n.
 template <class R>
-__global__ void y_kernel(Args<R> a, int n) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(g % a.S);
-    const int i = 3 + (int)(g / a.S);
-    if (i >= n) return;
-    R y = a.Z[i_z(i, n) * a.S + s];
-    for (int j = 3; j < i; ++j) y = fma(chi(a, j, s) * pp(a, i - 1, j + 1, s), a.Z5[i_z5(j, i, n) * a.S + s], y);
-    a.Y[(size_t)i * a.S + s] = y;
+__global__ void __launch_bounds__(ETB) y_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int i = 3 + blockIdx.y; i < n; i += gridDim.y) {
+        Spins<R> sp(a, s);
+        R y = a.Z[i_z(i, n) * a.S + s];
+        for (int j = 3; j < i; ++j) y = fma(sp(j) * pp(a, i - 1, j + 1, s), a.Z5[i_z5(j, i, n) * a.S + s], y);
+        a.Y[(size_t)i * a.S + s] = y;
+    }
 }
 
 template <class R, int K>
 __global__ void bias_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.S) return;
+    Spins<R> sp(a, s);
     const R Pm = a.P[(size_t)(n - 1) * a.S + s];
     R B = k1(a, n) * Pm;
     if (K == 3) {
         if (n >= 2) B += a.G[s];
-        for (int i = 2; i < n; ++i) B = fma(chi(a, i, s) * pp(a, n - 1, i + 1, s), a.Z[i_z(i, n) * a.S + s], B);
+        for (int i = 2; i < n; ++i) B = fma(sp(i) * pp(a, n - 1, i + 1, s), a.Z[i_z(i, n) * a.S + s], B);
     } else {
-        for (int i = 1; i < n; ++i) B = fma(k2(a, i, n) * chi(a, i, s), p1(a, n - 1, i, s), B);
+        for (int i = 1; i < n; ++i) B = fma(k2(a, i, n) * sp(i), p1(a, n - 1, i, s), B);
         if (n >= 3) B += a.G[s];
-        for (int i = 3; i < n; ++i) B = fma(chi(a, i, s) * pp(a, n - 1, i + 1, s), a.Y[(size_t)i * a.S + s], B);
+        for (int i = 3; i < n; ++i) B = fma(sp(i) * pp(a, n - 1, i + 1, s), a.Y[(size_t)i * a.S + s], B);
     }
     const R p0 = Pm + B, p1v = Pm - B;
     const R c0 = p0 > R(0) ? p0 : R(0), c1 = p1v > R(0) ? p1v : R(0);
@@ -334,99 +342,101 @@ __global__ void bias_kernel(Args<R> a, int n) {
 }
 
 // ---------------------------------------------------------------- step n: table rows
+// Thread per (entry, sample); the entry comes from blockIdx.y, so every index
+// below is uniform across a warp.
 
 // Order-3 part of the p+ update, factored: the term
 //   sum_{i > j >= l} kappa(j,i,n) chi_i chi_j chi_n Pp~[n-1][i+1] Pp~[i-1][j+1] Pp~[j-1][l]
 // equals chi_n sum_{j >= l} Pp~[j-1][l] v(j) with
 //   v(j) = chi_j sum_{i > j} kappa(j,i,n) chi_i Pp~[n-1][i+1] Pp~[i-1][j+1],
-// which does not depend on l. Thread per (j, sample); v goes to Y (free after the bias).
+// which does not depend on l. v goes to Y (free after the bias).
 template <class R>
-__global__ void pv_kernel(Args<R> a, int n) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(g % a.S);
-    const int j = 1 + (int)(g / a.S);
-    if (j >= n) return;
-    Spins<R> sp(a, s);
-    R v = R(0);
-    for (int i = j + 1; i < n; ++i) v = fma(k3(a, j, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, j + 1, s), v);
-    a.Y[(size_t)j * a.S + s] = v * sp(j);
+__global__ void __launch_bounds__(ETB) pv_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int j = 1 + blockIdx.y; j < n; j += gridDim.y) {
+        Spins<R> sp(a, s);
+        R v = R(0);
+        for (int i = j + 1; i < n; ++i)
+            v = fma(k3(a, j, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, j + 1, s), v);
+        a.Y[(size_t)j * a.S + s] = v * sp(j);
+    }
 }
 
-// Pp~[n][l], l = 1..n (Eq. a / Eq. probpartialade). Thread per (l, sample).
+// Pp~[n][l], l = 1..n (Eq. a / Eq. probpartialade).
 template <class R>
-__global__ void pp_kernel(Args<R> a, int n) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(g % a.S);
-    const int l = 1 + (int)(g / a.S);
-    if (l > n) return;
-    Spins<R> sp(a, s);
-    const R cn = sp(n);
-    R acc = R(0);
-    if (a.opp >= 2)
-        for (int i = l; i < n; ++i) acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), acc);
-    if (a.opp >= 3)
-        for (int j = l; j < n - 1; ++j) acc = fma(a.Y[(size_t)j * a.S + s], pp(a, j - 1, l, s), acc);
-    a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s));
+__global__ void __launch_bounds__(ETB) pp_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int l = 1 + blockIdx.y; l <= n; l += gridDim.y) {
+        Spins<R> sp(a, s);
+        const R cn = sp(n);
+        R acc = R(0);
+        if (a.opp >= 2)
+            for (int i = l; i < n; ++i)
+                acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), acc);
+        if (a.opp >= 3)
+            for (int j = l; j < n - 1; ++j) acc = fma(a.Y[(size_t)j * a.S + s], pp(a, j - 1, l, s), acc);
+        a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s));
+    }
 }
 
-// P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade). Thread per (e, sample).
+// P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade).
 // K = 5, order 3: with (a, b, c) the decreasing order of (i, j, e), the terms with
 // a = e come from the product rows (X_e(n), times Pp~[n-1][e+1]); the others
 // (a = i > e) are summed here over i, each with the factor chi_i Pp~[n-1][i+1].
 template <class R, int K>
-__global__ void p1_kernel(Args<R> a, int n) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(g % a.S);
-    const int e = 1 + (int)(g / a.S);
-    if (e >= n) return;
-    Spins<R> sp(a, s);
-    const R cn = sp(n);
-    R acc = R(0);
-    if (a.op1 >= 2)
-        for (int i = 1; i < n; ++i) {
-            if (i == e) continue;
-            const int hi = i > e ? i : e, lo = i > e ? e : i;
-            const R g2 = k2(a, i, n) * sp(i);
-            if (K == 3) acc = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), acc);
-            else acc = fma(g2, p2(a, n - 1, hi, lo, s), acc);
+__global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int e = 1 + blockIdx.y; e < n; e += gridDim.y) {
+        Spins<R> sp(a, s);
+        const R cn = sp(n);
+        R acc = R(0);
+        if (a.op1 >= 2)
+            for (int i = 1; i < n; ++i) {
+                if (i == e) continue;
+                const int hi = i > e ? i : e, lo = i > e ? e : i;
+                const R g2 = k2(a, i, n) * sp(i);
+                if (K == 3) acc = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), acc);
+                else acc = fma(g2, p2(a, n - 1, hi, lo, s), acc);
+            }
+        if (K == 5 && a.op1 >= 3) {
+            if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * a.S + s], acc);
+            for (int i = e + 1; i < n; ++i) {
+                R t = R(0);
+                Spins<R> sj(a, s);
+                // j < e: P2~[i-1][e][j]; j > e: P2~[i-1][j][e]
+                for (int j = 1; j < e; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, e, j, s), t);
+                for (int j = e + 1; j < i; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, j, e, s), t);
+                acc = fma(sp(i) * pp(a, n - 1, i + 1, s), t, acc);
+            }
         }
-    if (K == 5 && a.op1 >= 3) {
-        if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * a.S + s], acc);
-        for (int i = e + 1; i < n; ++i) {
-            R t = R(0);
-            // j < e: P2~[i-1][e][j]; j > e: P2~[i-1][j][e]
-            Spins<R> sj(a, s);
-            for (int j = 1; j < e; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, e, j, s), t);
-            for (int j = e + 1; j < i; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, j, e, s), t);
-            acc = fma(sp(i) * pp(a, n - 1, i + 1, s), t, acc);
-        }
+        a.P1[i_p1(n, e) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
     }
-    a.P1[i_p1(n, e) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
 }
 
-// P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade). Thread per ((e, d), sample).
+// P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade).
 // Order 2: i > e reaches P2~[i-1][e][d] (factor Pp~[n-1][i+1]); i < e reaches
 // P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]).
 template <class R>
-__global__ void p2_kernel(Args<R> a, int n) {
-    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = (int)(g % a.S);
-    const uint64_t r = g / a.S;
-    if (r >= cb(n - 1, 2)) return;
-    int hi, lo;
-    pair_of(r, hi, lo);
-    const int e = hi + 1, d = lo + 1;
-    Spins<R> sp(a, s);
-    const R cn = sp(n);
-    R acc = R(0);
-    if (a.op2 >= 2) {
-        R t = R(0);
-        for (int i = 1; i < d; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, d, i, s), t);
-        for (int i = d + 1; i < e; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, i, d, s), t);
-        acc = pp(a, n - 1, e + 1, s) * t;
-        for (int i = e + 1; i < n; ++i) acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), p2(a, i - 1, e, d, s), acc);
+__global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    const uint64_t nr = cb(n - 1, 2);
+    for (uint64_t r = blockIdx.y; r < nr; r += gridDim.y) {
+        int hi, lo;
+        pair_of(r, hi, lo);
+        const int e = hi + 1, d = lo + 1;
+        Spins<R> sp(a, s);
+        const R cn = sp(n);
+        R acc = R(0);
+        if (a.op2 >= 2) {
+            R t = R(0);
+            for (int i = 1; i < d; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, d, i, s), t);
+            for (int i = d + 1; i < e; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, i, d, s), t);
+            acc = pp(a, n - 1, e + 1, s) * t;
+            for (int i = e + 1; i < n; ++i)
+                acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), p2(a, i - 1, e, d, s), acc);
+        }
+        a.P2[i_p2(n, e, d) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
     }
-    a.P2[i_p2(n, e, d) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
 }
 
 template <class R>
@@ -473,6 +483,7 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.G, 1);
     take(L.Y, K == 5 ? (size_t)M + 1 : 0);
     take(L.X, K == 5 ? cb(M, 2) : 0);
+    take(L.W, K == 5 ? cb(M - 1, 2) : (size_t)M);
     L.bw = off;
     off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
     L.kap = off;
@@ -483,40 +494,32 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     return L;
 }
 
+// Grid of a per-(entry, sample) kernel: samples along x, entries along y.
+static dim3 egrid(int S, uint64_t entries) {
+    return dim3((unsigned)(S / ETB), (unsigned)(entries < 65535 ? (entries > 0 ? entries : 1) : 65535));
+}
+
 template <class R, int K>
 static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
     const int S = a.S, M = a.M;
     const int TB = 256;
+    constexpr int TM = sizeof(R) == 4 ? 8 : 4, TN = TM;
     init_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a);
     for (int t = 1; t <= M; ++t) {
         // products for this step and later ones (inputs: rows < t of the tables)
         const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);
         if (D > 0) {
+            w_kernel<R, K><<<egrid(S, (uint64_t)D), ETB, 0, st>>>(a, t, D);
             const uint64_t rows = K == 3 ? 1 + (uint64_t)(M - t) : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
-            dim3 grid((unsigned)((rows + BM - 1) / BM), (unsigned)(S / BN));
-            zgemm_kernel<R, K><<<grid, 256, 0, st>>>(a, t, rows, D);
+            dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
+            zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
         }
-        if (K == 5 && t > 3) {
-            const uint64_t nt = (uint64_t)(t - 3) * S;
-            y_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
-        }
+        if (K == 5 && t > 3) y_kernel<R><<<egrid(S, (uint64_t)(t - 3)), ETB, 0, st>>>(a, t);
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
-        if (K == 5 && a.opp >= 3 && t > 1) {
-            const uint64_t nt = (uint64_t)(t - 1) * S;
-            pv_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
-        }
-        {
-            const uint64_t nt = (uint64_t)t * S;
-            pp_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
-        }
-        if (t > 1) {
-            const uint64_t nt = (uint64_t)(t - 1) * S;
-            p1_kernel<R, K><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
-        }
-        if (K == 5 && t > 2) {
-            const uint64_t nt = cb(t - 1, 2) * S;
-            p2_kernel<R><<<(unsigned)((nt + TB - 1) / TB), TB, 0, st>>>(a, t);
-        }
+        if (K == 5 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
+        if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        if (K == 5 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -547,6 +550,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.G = reinterpret_cast<R *>(w + L.G);
     a.Y = reinterpret_cast<R *>(w + L.Y);
     a.X = reinterpret_cast<R *>(w + L.X);
+    a.W = reinterpret_cast<R *>(w + L.W);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
     if (sizeof(R) == sizeof(double)) {
         a.kap = reinterpret_cast<const R *>(c.kappa);
@@ -596,7 +600,7 @@ bool dev_ptr(const void *p) {
 }
 
 bool valid_shape(int M, int K, int batch, int precision) {
-    return (K == 3 || K == 5) && M >= K && M <= GBS_MAX_MODES && batch >= 64 && batch % 64 == 0 &&
+    return (K == 3 || K == 5) && M >= K && M <= GBS_MAX_MODES && batch >= 128 && batch % 128 == 0 &&
            (precision == GBS_SAMPLE_FP64 || precision == GBS_SAMPLE_FP32);
 }
 
@@ -615,7 +619,7 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
     using gbs::record_error;
     if (!valid_shape(M, K, batch, precision))
         return record_error(GBS_ERR_INVALID_ARG,
-                            "need K in {3, 5}, K <= M <= 1024, batch a positive multiple of 64 and precision "
+                            "need K in {3, 5}, K <= M <= 1024, batch a positive multiple of 128 and precision "
                             "GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
     if (n_samples < 0) return record_error(GBS_ERR_INVALID_ARG, "n_samples must be >= 0");
     int ord[3] = {3, 3, 2};

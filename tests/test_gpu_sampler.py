@@ -34,9 +34,9 @@ def uniforms(n, M, seed):
     return np.random.default_rng(seed).random((n, M))
 
 
-@pytest.mark.parametrize("K,M,orders,n,batch", [(3, 12, None, 200, 64), (5, 14, None, 200, 128),
-                                                (5, 13, (2, 2, 1), 130, 64), (5, 9, (3, 2, 1), 64, 64),
-                                                (3, 3, None, 64, 64), (5, 5, None, 64, 64)])
+@pytest.mark.parametrize("K,M,orders,n,batch", [(3, 12, None, 300, 128), (5, 14, None, 200, 128),
+                                                (5, 13, (2, 2, 1), 130, 128), (5, 9, (3, 2, 1), 64, 128),
+                                                (3, 3, None, 64, 128), (5, 5, None, 260, 128)])
 def test_fp64_draws_match_oracle(K, M, orders, n, batch):
     inst = synthetic.random_instance(M, K, seed=500 + M + K, r_range=(0.5, 1.3))
     kap = kappa_of(inst, K)
@@ -85,7 +85,7 @@ def test_fp32_m144_k5_consistent_on_a_few_samples():
     kap = kappa_of(inst, 5)
     n = 64
     u = uniforms(n, 144, seed=144)
-    bits, prob, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=64, precision="fp32",
+    bits, prob, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
                                 want_q0=True)
     assert bool(torch.isfinite(prob).all()) and bool((prob > 0).all())
     b = bits.cpu().numpy()[:2]
@@ -101,8 +101,9 @@ def test_invalid_arguments():
     kap = kappa_of(inst, 5)
     u = torch.rand(4, 8, dtype=torch.float64, device="cuda")
     with pytest.raises(gbs.GbsError):
-        gbs.sample(kap, 8, 5, u=u, batch=48)
+        gbs.sample(kap, 8, 5, u=u, batch=64)
     with pytest.raises(gbs.GbsError):
         gbs.sample(kap, 8, 5, u=u, orders=(4, 3, 2))
-    assert gbs.sampler_workspace_bytes(8, 4, 64) == 0
-    assert gbs.sampler_workspace_bytes(4, 5, 64) == 0
+    assert gbs.sampler_workspace_bytes(8, 4, 128) == 0
+    assert gbs.sampler_workspace_bytes(4, 5, 128) == 0
+    assert gbs.sampler_workspace_bytes(8, 5, 64) == 0
