@@ -383,9 +383,12 @@ __global__ void __launch_bounds__(ETB) pp_kernel(Args<R> a, int n) {
 // K = 5, order 3: with (a, b, c) the decreasing order of (i, j, e), the terms with
 // a = e come from the product rows (X_e(n), times Pp~[n-1][e+1]); the others
 // (a = i > e) are summed here over i, each with the factor chi_i Pp~[n-1][i+1].
+// The inner loops walk P2~ row i-1 by running offsets; the boundary entries
+// (P2~[i-1][i-1][.] = P1~[i-2][.], P1~[i-2][i-2] = P~[i-3]) are taken apart.
 template <class R, int K>
 __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
+    const size_t S = (size_t)a.S;
     for (int e = 1 + blockIdx.y; e < n; e += gridDim.y) {
         Spins<R> sp(a, s);
         const R cn = sp(n);
@@ -399,27 +402,49 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
                 else acc = fma(g2, p2(a, n - 1, hi, lo, s), acc);
             }
         if (K == 5 && a.op1 >= 3) {
-            if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * a.S + s], acc);
+            if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * S + s], acc);
+            const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
             for (int i = e + 1; i < n; ++i) {
-                R t = R(0);
+                const R *kp = a.kap + a.off[3] + cb(n - 1, 3) + cb(i - 1, 2) - 1;  // kp[j] = kappa(j, i, n)
                 Spins<R> sj(a, s);
-                // j < e: P2~[i-1][e][j]; j > e: P2~[i-1][j][e]
-                for (int j = 1; j < e; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, e, j, s), t);
-                for (int j = e + 1; j < i; ++j) t = fma(k3(a, j, i, n) * sj(j), p2(a, i - 1, j, e, s), t);
+                R t = R(0);
+                // j < e: P2~[i-1][e][j]
+                if (e < i - 1) {
+                    const R *q = P2 + i_p2(i - 1, e, 1) * S;
+#pragma unroll 4
+                    for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), *q, t);
+                } else {
+                    const R *q = P1 + (i >= 3 ? i_p1(i - 2, 1) : 0) * S;
+                    for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), j == i - 2 ? P[(size_t)(i - 3) * S] : *q, t);
+                }
+                // e < j < i: P2~[i-1][j][e]
+                if (e + 1 <= i - 2) {
+                    uint64_t idx = i_p2(i - 1, e + 1, e);
+#pragma unroll 4
+                    for (int j = e + 1; j < i - 1; ++j) {
+                        t = fma(kp[j] * sj(j), P2[idx * S], t);
+                        idx += (uint64_t)(j - 1);
+                    }
+                }
+                if (e < i - 1) t = fma(kp[i - 1] * sj(i - 1), e == i - 2 ? P[(size_t)(i - 3) * S] : P1[i_p1(i - 2, e) * S], t);
                 acc = fma(sp(i) * pp(a, n - 1, i + 1, s), t, acc);
             }
         }
-        a.P1[i_p1(n, e) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
+        a.P1[i_p1(n, e) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
     }
 }
 
 // P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade).
 // Order 2: i > e reaches P2~[i-1][e][d] (factor Pp~[n-1][i+1]); i < e reaches
-// P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]).
+// P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]). Running offsets as
+// in p1_kernel.
 template <class R>
 __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
+    const size_t S = (size_t)a.S;
     const uint64_t nr = cb(n - 1, 2);
+    const R *kp = a.kap + a.off[2] + cb(n - 1, 2) - 1;  // kp[i] = kappa(i, n)
+    const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
     for (uint64_t r = blockIdx.y; r < nr; r += gridDim.y) {
         int hi, lo;
         pair_of(r, hi, lo);
@@ -429,13 +454,39 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
         R acc = R(0);
         if (a.op2 >= 2) {
             R t = R(0);
-            for (int i = 1; i < d; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, d, i, s), t);
-            for (int i = d + 1; i < e; ++i) t = fma(k2(a, i, n) * sp(i), p2(a, e - 1, i, d, s), t);
+            // i < d: P2~[e-1][d][i]
+            if (d < e - 1) {
+                const R *q = P2 + i_p2(e - 1, d, 1) * S;
+#pragma unroll 4
+                for (int i = 1; i < d; ++i, q += S) t = fma(kp[i] * sp(i), *q, t);
+            } else {
+                const R *q = P1 + (e >= 3 ? i_p1(e - 2, 1) : 0) * S;
+                for (int i = 1; i < d; ++i, q += S) t = fma(kp[i] * sp(i), i == e - 2 ? P[(size_t)(e - 3) * S] : *q, t);
+            }
+            // d < i < e: P2~[e-1][i][d]
+            if (d + 1 <= e - 2) {
+                uint64_t idx = i_p2(e - 1, d + 1, d);
+#pragma unroll 4
+                for (int i = d + 1; i < e - 1; ++i) {
+                    t = fma(kp[i] * sp(i), P2[idx * S], t);
+                    idx += (uint64_t)(i - 1);
+                }
+            }
+            if (d < e - 1) t = fma(kp[e - 1] * sp(e - 1), d == e - 2 ? P[(size_t)(e - 3) * S] : P1[i_p1(e - 2, d) * S], t);
             acc = pp(a, n - 1, e + 1, s) * t;
-            for (int i = e + 1; i < n; ++i)
-                acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), p2(a, i - 1, e, d, s), acc);
+            // i > e: P2~[i-1][e][d] (i = e + 1: P1~[e-1][d], or P~[e-2] when d = e - 1)
+            if (e + 1 < n) {
+                acc = fma(kp[e + 1] * sp(e + 1) * pp(a, n - 1, e + 2, s),
+                          d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S], acc);
+                uint64_t idx = i_p2(e + 1, e, d);
+#pragma unroll 4
+                for (int i = e + 2; i < n; ++i) {
+                    acc = fma(kp[i] * sp(i) * pp(a, n - 1, i + 1, s), P2[idx * S], acc);
+                    idx += cb(i - 2, 2);
+                }
+            }
         }
-        a.P2[i_p2(n, e, d) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
+        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
     }
 }
 
