@@ -73,6 +73,8 @@ struct Args {
     uint64_t off[6];       // order offsets of the cumulant table
     int M, K, S, opp, op1, op2;
     R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X, *W;
+    R *CA, *CB, *CC;       // per-step coefficients [i][S]: chi_i Pp~[n-1][i+1], kappa(i,n) chi_i, kappa(i,n) chi_i Pp~[n-1][i+1]
+    R *PT;                 // [P1CH][M][S] partial sums of the p1 order-3 term
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -379,12 +381,79 @@ __global__ void __launch_bounds__(ETB) pp_kernel(Args<R> a, int n) {
     }
 }
 
+// Per-step coefficients of the table updates, one per (i < n, sample):
+//   CA = chi_i Pp~[n-1][i+1],  CB = kappa(i,n) chi_i,  CC = kappa(i,n) chi_i Pp~[n-1][i+1].
+template <class R>
+__global__ void __launch_bounds__(ETB) coef_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    for (int i = 1 + blockIdx.y; i < n; i += gridDim.y) {
+        Spins<R> sp(a, s);
+        const R ppv = pp(a, n - 1, i + 1, s), cbv = k2(a, i, n) * sp(i);
+        const size_t o = (size_t)i * a.S + s;
+        a.CA[o] = sp(i) * ppv;
+        a.CB[o] = cbv;
+        a.CC[o] = cbv * ppv;
+    }
+}
+
+constexpr int P1CH = 8;  // chunks of the i range of the p1 order-3 term
+
+// First index of chunk c of the range i = e+1 .. n-1, cut so that every chunk
+// holds about the same number of inner terms (about i per i).
+__device__ __forceinline__ int p1_chunk_start(int e, int n, int c) {
+    if (c <= 0) return e + 1;
+    if (c >= P1CH) return n;
+    const double lo = (double)(e + 1) * (e + 1), hi = (double)n * n;
+    int i = (int)ceil(sqrt(lo + (hi - lo) * (double)c / P1CH));
+    return i < e + 1 ? e + 1 : (i > n ? n : i);
+}
+
+// K = 5, p1 order 3, the terms with largest index i > e, for the i of one chunk:
+// PT[c][e][s] = sum_{i in chunk c} CA[i] sum_{j < i, j != e} kappa(j,i,n) chi_j P2~[i-1][{j, e}].
+// The inner loops walk P2~ row i-1 by running offsets; the boundary entries
+// (P2~[i-1][i-1][.] = P1~[i-2][.], P1~[i-2][i-2] = P~[i-3]) are taken apart.
+template <class R>
+__global__ void __launch_bounds__(ETB) p1o3_kernel(Args<R> a, int n) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    const size_t S = (size_t)a.S;
+    const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
+    for (int y = blockIdx.y; y < (n - 1) * P1CH; y += gridDim.y) {
+        const int e = 1 + y / P1CH, c = y % P1CH;
+        const int i0 = p1_chunk_start(e, n, c), i1 = p1_chunk_start(e, n, c + 1);
+        R acc = R(0);
+        for (int i = i0; i < i1; ++i) {
+            const R *kp = a.kap + a.off[3] + cb(n - 1, 3) + cb(i - 1, 2) - 1;  // kp[j] = kappa(j, i, n)
+            Spins<R> sj(a, s);
+            R t = R(0);
+            // j < e: P2~[i-1][e][j]
+            if (e < i - 1) {
+                const R *q = P2 + i_p2(i - 1, e, 1) * S;
+#pragma unroll 4
+                for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), *q, t);
+            } else {
+                const R *q = P1 + (i >= 3 ? i_p1(i - 2, 1) : 0) * S;
+                for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), j == i - 2 ? P[(size_t)(i - 3) * S] : *q, t);
+            }
+            // e < j < i: P2~[i-1][j][e]
+            if (e + 1 <= i - 2) {
+                uint64_t idx = i_p2(i - 1, e + 1, e);
+#pragma unroll 4
+                for (int j = e + 1; j < i - 1; ++j) {
+                    t = fma(kp[j] * sj(j), P2[idx * S], t);
+                    idx += (uint64_t)(j - 1);
+                }
+            }
+            if (e < i - 1) t = fma(kp[i - 1] * sj(i - 1), e == i - 2 ? P[(size_t)(i - 3) * S] : P1[i_p1(i - 2, e) * S], t);
+            acc = fma(a.CA[(size_t)i * S + s], t, acc);
+        }
+        a.PT[((size_t)c * a.M + e) * S + s] = acc;
+    }
+}
+
 // P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade).
 // K = 5, order 3: with (a, b, c) the decreasing order of (i, j, e), the terms with
 // a = e come from the product rows (X_e(n), times Pp~[n-1][e+1]); the others
-// (a = i > e) are summed here over i, each with the factor chi_i Pp~[n-1][i+1].
-// The inner loops walk P2~ row i-1 by running offsets; the boundary entries
-// (P2~[i-1][i-1][.] = P1~[i-2][.], P1~[i-2][i-2] = P~[i-3]) are taken apart.
+// (a = i > e) come from the chunk partial sums of p1o3_kernel.
 template <class R, int K>
 __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
@@ -403,32 +472,8 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
             }
         if (K == 5 && a.op1 >= 3) {
             if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * S + s], acc);
-            const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
-            for (int i = e + 1; i < n; ++i) {
-                const R *kp = a.kap + a.off[3] + cb(n - 1, 3) + cb(i - 1, 2) - 1;  // kp[j] = kappa(j, i, n)
-                Spins<R> sj(a, s);
-                R t = R(0);
-                // j < e: P2~[i-1][e][j]
-                if (e < i - 1) {
-                    const R *q = P2 + i_p2(i - 1, e, 1) * S;
-#pragma unroll 4
-                    for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), *q, t);
-                } else {
-                    const R *q = P1 + (i >= 3 ? i_p1(i - 2, 1) : 0) * S;
-                    for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), j == i - 2 ? P[(size_t)(i - 3) * S] : *q, t);
-                }
-                // e < j < i: P2~[i-1][j][e]
-                if (e + 1 <= i - 2) {
-                    uint64_t idx = i_p2(i - 1, e + 1, e);
-#pragma unroll 4
-                    for (int j = e + 1; j < i - 1; ++j) {
-                        t = fma(kp[j] * sj(j), P2[idx * S], t);
-                        idx += (uint64_t)(j - 1);
-                    }
-                }
-                if (e < i - 1) t = fma(kp[i - 1] * sj(i - 1), e == i - 2 ? P[(size_t)(i - 3) * S] : P1[i_p1(i - 2, e) * S], t);
-                acc = fma(sp(i) * pp(a, n - 1, i + 1, s), t, acc);
-            }
+#pragma unroll
+            for (int c = 0; c < P1CH; ++c) acc += a.PT[((size_t)c * a.M + e) * S + s];
         }
         a.P1[i_p1(n, e) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
     }
@@ -443,7 +488,6 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
     const size_t S = (size_t)a.S;
     const uint64_t nr = cb(n - 1, 2);
-    const R *kp = a.kap + a.off[2] + cb(n - 1, 2) - 1;  // kp[i] = kappa(i, n)
     const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
     for (uint64_t r = blockIdx.y; r < nr; r += gridDim.y) {
         int hi, lo;
@@ -454,34 +498,34 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
         R acc = R(0);
         if (a.op2 >= 2) {
             R t = R(0);
+            const R *CB = a.CB + s, *CC = a.CC + s;
             // i < d: P2~[e-1][d][i]
             if (d < e - 1) {
                 const R *q = P2 + i_p2(e - 1, d, 1) * S;
 #pragma unroll 4
-                for (int i = 1; i < d; ++i, q += S) t = fma(kp[i] * sp(i), *q, t);
+                for (int i = 1; i < d; ++i, q += S) t = fma(CB[i * S], *q, t);
             } else {
                 const R *q = P1 + (e >= 3 ? i_p1(e - 2, 1) : 0) * S;
-                for (int i = 1; i < d; ++i, q += S) t = fma(kp[i] * sp(i), i == e - 2 ? P[(size_t)(e - 3) * S] : *q, t);
+                for (int i = 1; i < d; ++i, q += S) t = fma(CB[i * S], i == e - 2 ? P[(size_t)(e - 3) * S] : *q, t);
             }
             // d < i < e: P2~[e-1][i][d]
             if (d + 1 <= e - 2) {
                 uint64_t idx = i_p2(e - 1, d + 1, d);
 #pragma unroll 4
                 for (int i = d + 1; i < e - 1; ++i) {
-                    t = fma(kp[i] * sp(i), P2[idx * S], t);
+                    t = fma(CB[i * S], P2[idx * S], t);
                     idx += (uint64_t)(i - 1);
                 }
             }
-            if (d < e - 1) t = fma(kp[e - 1] * sp(e - 1), d == e - 2 ? P[(size_t)(e - 3) * S] : P1[i_p1(e - 2, d) * S], t);
+            if (d < e - 1) t = fma(CB[(e - 1) * S], d == e - 2 ? P[(size_t)(e - 3) * S] : P1[i_p1(e - 2, d) * S], t);
             acc = pp(a, n - 1, e + 1, s) * t;
             // i > e: P2~[i-1][e][d] (i = e + 1: P1~[e-1][d], or P~[e-2] when d = e - 1)
             if (e + 1 < n) {
-                acc = fma(kp[e + 1] * sp(e + 1) * pp(a, n - 1, e + 2, s),
-                          d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S], acc);
+                acc = fma(CC[(e + 1) * S], d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S], acc);
                 uint64_t idx = i_p2(e + 1, e, d);
 #pragma unroll 4
                 for (int i = e + 2; i < n; ++i) {
-                    acc = fma(kp[i] * sp(i) * pp(a, n - 1, i + 1, s), P2[idx * S], acc);
+                    acc = fma(CC[i * S], P2[idx * S], acc);
                     idx += cb(i - 2, 2);
                 }
             }
@@ -535,6 +579,8 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.Y, K == 5 ? (size_t)M + 1 : 0);
     take(L.X, K == 5 ? cb(M, 2) : 0);
     take(L.W, K == 5 ? cb(M - 1, 2) : (size_t)M);
+    take(L.CA, K == 5 ? 3 * ((size_t)M + 1) : 0);
+    take(L.PT, K == 5 ? (size_t)P1CH * M : 0);
     L.bw = off;
     off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
     L.kap = off;
@@ -569,6 +615,8 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
         if (K == 5 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
+        if (K == 5 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        if (K == 5 && a.op1 >= 3 && t > 1) p1o3_kernel<R><<<egrid(S, (uint64_t)(t - 1) * P1CH), ETB, 0, st>>>(a, t);
         if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         if (K == 5 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);
         cudaError_t e = cudaGetLastError();
@@ -602,6 +650,10 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.Y = reinterpret_cast<R *>(w + L.Y);
     a.X = reinterpret_cast<R *>(w + L.X);
     a.W = reinterpret_cast<R *>(w + L.W);
+    a.CA = reinterpret_cast<R *>(w + L.CA);
+    a.CB = a.CA + ((size_t)c.M + 1) * c.S;
+    a.CC = a.CB + ((size_t)c.M + 1) * c.S;
+    a.PT = reinterpret_cast<R *>(w + L.PT);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
     if (sizeof(R) == sizeof(double)) {
         a.kap = reinterpret_cast<const R *>(c.kappa);
