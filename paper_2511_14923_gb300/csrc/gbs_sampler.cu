@@ -74,7 +74,7 @@ struct Args {
     int M, K, S, opp, op1, op2;
     R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X, *W;
     R *CA, *CB, *CC;       // per-step coefficients [i][S]: chi_i Pp~[n-1][i+1], kappa(i,n) chi_i, kappa(i,n) chi_i Pp~[n-1][i+1]
-    R *PT;                 // [P1CH][M][S] partial sums of the p1 order-3 term
+    R *T;                  // [C(M,2)][2][S] per-pair parts of the p1 order-3 term (see p2_kernel)
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -396,64 +396,10 @@ __global__ void __launch_bounds__(ETB) coef_kernel(Args<R> a, int n) {
     }
 }
 
-constexpr int P1CH = 8;  // chunks of the i range of the p1 order-3 term
-
-// First index of chunk c of the range i = e+1 .. n-1, cut so that every chunk
-// holds about the same number of inner terms (about i per i).
-__device__ __forceinline__ int p1_chunk_start(int e, int n, int c) {
-    if (c <= 0) return e + 1;
-    if (c >= P1CH) return n;
-    const double lo = (double)(e + 1) * (e + 1), hi = (double)n * n;
-    int i = (int)ceil(sqrt(lo + (hi - lo) * (double)c / P1CH));
-    return i < e + 1 ? e + 1 : (i > n ? n : i);
-}
-
-// K = 5, p1 order 3, the terms with largest index i > e, for the i of one chunk:
-// PT[c][e][s] = sum_{i in chunk c} CA[i] sum_{j < i, j != e} kappa(j,i,n) chi_j P2~[i-1][{j, e}].
-// The inner loops walk P2~ row i-1 by running offsets; the boundary entries
-// (P2~[i-1][i-1][.] = P1~[i-2][.], P1~[i-2][i-2] = P~[i-3]) are taken apart.
-template <class R>
-__global__ void __launch_bounds__(ETB) p1o3_kernel(Args<R> a, int n) {
-    const int s = blockIdx.x * ETB + threadIdx.x;
-    const size_t S = (size_t)a.S;
-    const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
-    for (int y = blockIdx.y; y < (n - 1) * P1CH; y += gridDim.y) {
-        const int e = 1 + y / P1CH, c = y % P1CH;
-        const int i0 = p1_chunk_start(e, n, c), i1 = p1_chunk_start(e, n, c + 1);
-        R acc = R(0);
-        for (int i = i0; i < i1; ++i) {
-            const R *kp = a.kap + a.off[3] + cb(n - 1, 3) + cb(i - 1, 2) - 1;  // kp[j] = kappa(j, i, n)
-            Spins<R> sj(a, s);
-            R t = R(0);
-            // j < e: P2~[i-1][e][j]
-            if (e < i - 1) {
-                const R *q = P2 + i_p2(i - 1, e, 1) * S;
-#pragma unroll 4
-                for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), *q, t);
-            } else {
-                const R *q = P1 + (i >= 3 ? i_p1(i - 2, 1) : 0) * S;
-                for (int j = 1; j < e; ++j, q += S) t = fma(kp[j] * sj(j), j == i - 2 ? P[(size_t)(i - 3) * S] : *q, t);
-            }
-            // e < j < i: P2~[i-1][j][e]
-            if (e + 1 <= i - 2) {
-                uint64_t idx = i_p2(i - 1, e + 1, e);
-#pragma unroll 4
-                for (int j = e + 1; j < i - 1; ++j) {
-                    t = fma(kp[j] * sj(j), P2[idx * S], t);
-                    idx += (uint64_t)(j - 1);
-                }
-            }
-            if (e < i - 1) t = fma(kp[i - 1] * sj(i - 1), e == i - 2 ? P[(size_t)(i - 3) * S] : P1[i_p1(i - 2, e) * S], t);
-            acc = fma(a.CA[(size_t)i * S + s], t, acc);
-        }
-        a.PT[((size_t)c * a.M + e) * S + s] = acc;
-    }
-}
-
 // P1~[n][e], e = 1..n-1 (Eq. b / Eq. probelidedade).
 // K = 5, order 3: with (a, b, c) the decreasing order of (i, j, e), the terms with
 // a = e come from the product rows (X_e(n), times Pp~[n-1][e+1]); the others
-// (a = i > e) come from the chunk partial sums of p1o3_kernel.
+// (a = i > e) from the per-pair sums p2_kernel leaves in T.
 template <class R, int K>
 __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
@@ -472,8 +418,11 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
             }
         if (K == 5 && a.op1 >= 3) {
             if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * S + s], acc);
-#pragma unroll
-            for (int c = 0; c < P1CH; ++c) acc += a.PT[((size_t)c * a.M + e) * S + s];
+            // pairs (e, d), d < e, carry chi_d-weighted parts for e; pairs (j, e), j > e, for e
+            const R *T = a.T + s;
+            Spins<R> sd(a, s);
+            for (int d = 1; d < e; ++d) acc = fma(sd(d), T[(2 * (cb(e - 1, 2) + (uint64_t)(d - 1))) * S], acc);
+            for (int j = e + 1; j < n; ++j) acc = fma(sd(j), T[(2 * (cb(j - 1, 2) + (uint64_t)(e - 1)) + 1) * S], acc);
         }
         a.P1[i_p1(n, e) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
     }
@@ -481,8 +430,14 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
 
 // P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade).
 // Order 2: i > e reaches P2~[i-1][e][d] (factor Pp~[n-1][i+1]); i < e reaches
-// P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]). Running offsets as
-// in p1_kernel.
+// P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]). The loops walk the
+// p2 rows by running offsets; the boundary entries (P2~[i-1][i-1][.] =
+// P1~[i-2][.], P1~[i-2][i-2] = P~[i-3]) are taken apart.
+// The same values P2~[i-1][e][d], i > e, are every term of the p1 order-3 sums
+// whose largest index is i (Eq. probelidedade with (a, b, c) = (i, e, d)): they
+// enter P1~[n][e] with weight CA[i] kappa(d,i,n) chi_d and P1~[n][d] with weight
+// CA[i] kappa(e,i,n) chi_e. Both sums are formed here, without chi_d / chi_e, and
+// left in T for p1_kernel, so each value is read once per step.
 template <class R>
 __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
     const int s = blockIdx.x * ETB + threadIdx.x;
@@ -519,16 +474,38 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
             }
             if (d < e - 1) t = fma(CB[(e - 1) * S], d == e - 2 ? P[(size_t)(e - 3) * S] : P1[i_p1(e - 2, d) * S], t);
             acc = pp(a, n - 1, e + 1, s) * t;
+        }
+        R tE = R(0), tD = R(0);
+        if ((a.op2 >= 2 || a.op1 >= 3) && e + 1 < n) {
+            const R *CA = a.CA + s, *CC = a.CC + s;
+            const R *k3n = a.kap + a.off[3] + cb(n - 1, 3) - 1;  // k3n[C(i-1,2) + j] = kappa(j, i, n)
+            R a2 = R(0);
             // i > e: P2~[i-1][e][d] (i = e + 1: P1~[e-1][d], or P~[e-2] when d = e - 1)
-            if (e + 1 < n) {
-                acc = fma(CC[(e + 1) * S], d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S], acc);
-                uint64_t idx = i_p2(e + 1, e, d);
-#pragma unroll 4
-                for (int i = e + 2; i < n; ++i) {
-                    acc = fma(CC[i * S], P2[idx * S], acc);
-                    idx += cb(i - 2, 2);
-                }
+            {
+                const R v = d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S];
+                const R *kp = k3n + cb(e, 2);
+                const R ca = CA[(e + 1) * S];
+                a2 = CC[(e + 1) * S] * v;
+                tE = ca * kp[d] * v;
+                tD = ca * kp[e] * v;
             }
+            uint64_t idx = i_p2(e + 1, e, d);
+#pragma unroll 4
+            for (int i = e + 2; i < n; ++i) {
+                const R v = P2[idx * S];
+                const R *kp = k3n + cb(i - 1, 2);
+                const R ca = CA[i * S];
+                a2 = fma(CC[i * S], v, a2);
+                tE = fma(ca * kp[d], v, tE);
+                tD = fma(ca * kp[e], v, tD);
+                idx += cb(i - 2, 2);
+            }
+            if (a.op2 >= 2) acc += a2;
+        }
+        if (a.op1 >= 3) {
+            const uint64_t o = 2 * r;
+            a.T[o * S + s] = tE;
+            a.T[(o + 1) * S + s] = tD;
         }
         a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
     }
@@ -580,7 +557,7 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.X, K == 5 ? cb(M, 2) : 0);
     take(L.W, K == 5 ? cb(M - 1, 2) : (size_t)M);
     take(L.CA, K == 5 ? 3 * ((size_t)M + 1) : 0);
-    take(L.PT, K == 5 ? (size_t)P1CH * M : 0);
+    take(L.T, K == 5 ? 2 * cb(M - 1, 2) : 0);
     L.bw = off;
     off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
     L.kap = off;
@@ -591,9 +568,15 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     return L;
 }
 
-// Grid of a per-(entry, sample) kernel: samples along x, entries along y.
+// Grid of a per-(entry, sample) kernel: samples along x, entries along y, about
+// 10^4 blocks in all (each block loops over its share of the entries).
 static dim3 egrid(int S, uint64_t entries) {
-    return dim3((unsigned)(S / ETB), (unsigned)(entries < 65535 ? (entries > 0 ? entries : 1) : 65535));
+    const uint64_t bx = (uint64_t)(S / ETB);
+    uint64_t cap = 10000 / bx;
+    if (cap < 16) cap = 16;
+    uint64_t by = entries < cap ? entries : cap;
+    if (by < 1) by = 1;
+    return dim3((unsigned)bx, (unsigned)by);
 }
 
 template <class R, int K>
@@ -616,9 +599,8 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         if (K == 5 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
         if (K == 5 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
-        if (K == 5 && a.op1 >= 3 && t > 1) p1o3_kernel<R><<<egrid(S, (uint64_t)(t - 1) * P1CH), ETB, 0, st>>>(a, t);
+        if (K == 5 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);  // before p1: fills T
         if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
-        if (K == 5 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -653,7 +635,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.CA = reinterpret_cast<R *>(w + L.CA);
     a.CB = a.CA + ((size_t)c.M + 1) * c.S;
     a.CC = a.CB + ((size_t)c.M + 1) * c.S;
-    a.PT = reinterpret_cast<R *>(w + L.PT);
+    a.T = reinterpret_cast<R *>(w + L.T);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
     if (sizeof(R) == sizeof(double)) {
         a.kap = reinterpret_cast<const R *>(c.kappa);
