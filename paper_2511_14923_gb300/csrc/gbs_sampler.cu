@@ -195,17 +195,41 @@ constexpr int ETB = 64;  // threads per block of the per-(entry, sample) kernels
 template <class R, int K>
 __global__ void __launch_bounds__(ETB) w_kernel(Args<R> a, int t, int D) {
     const int s = blockIdx.x * ETB + threadIdx.x;
-    for (int r = blockIdx.y; r < D; r += gridDim.y) {
-        R v;
-        if (K == 3) {
+    const size_t S = (size_t)a.S;
+    // this block's share of r = 0 .. D-1, walked in order
+    const int per = (D + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int r0 = blockIdx.y * per, r1 = r0 + per < D ? r0 + per : D;
+    if (r0 >= r1) return;
+    Spins<R> sp(a, s);
+    R *W = a.W + s;
+    if (K == 3) {
+        // W_t(d) = chi_d P1~[t-1][d], d = r + 1; d = t - 1 -> P~[t-2]
+        const R *q = a.P1 + (t >= 3 ? i_p1(t - 1, 1) : 0) * S + s;
+        for (int r = r0; r < r1; ++r) {
             const int d = r + 1;
-            v = p1(a, t - 1, d, s) * chi(a, d, s);
-        } else {
-            int hi, lo;
-            pair_of((uint64_t)r, hi, lo);
-            v = p2(a, t - 1, hi + 1, lo + 1, s) * chi(a, hi + 1, s) * chi(a, lo + 1, s);
+            const R v = d == t - 1 ? a.P[(size_t)(t - 2) * S + s] : q[(size_t)r * S];
+            W[(size_t)r * S] = v * sp(d);
         }
-        a.W[(size_t)r * a.S + s] = v;
+        return;
+    }
+    // K = 5: pair r = (e, d); for e < t - 1 the p2 row t - 1 holds the same pairs in
+    // the same order (offset C(t-2, 3)); e = t - 1 comes from P1~[t-2][d] (P~[t-3]
+    // when d = t - 2)
+    int hi, lo;
+    pair_of((uint64_t)r0, hi, lo);
+    int e = hi + 1, d = lo + 1;
+    Spins<R> sd(a, s);
+    const uint64_t rowlen = cb(t - 2, 2);
+    const R *q2 = a.P2 + (t >= 4 ? cb(t - 2, 3) : 0) * S + s;
+    for (int r = r0; r < r1; ++r) {
+        R v;
+        if ((uint64_t)r < rowlen) v = q2[(size_t)r * S];
+        else v = d == t - 2 ? a.P[(size_t)(t - 3) * S + s] : a.P1[i_p1(t - 2, d) * S + s];
+        W[(size_t)r * S] = v * sp(e) * sd(d);
+        if (++d == e) {
+            ++e;
+            d = 1;
+        }
     }
 }
 
