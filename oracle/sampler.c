@@ -19,7 +19,7 @@
  *     Pp[a][b]  = p+(x_a..x_b)        (all of b..a)
  *   double elision, K = 5 (App. "Approximating marginals efficiently with a chain
  *   rule": Eq. probade, Eq. probpartialade, Eq. probelidedade, Eq.
- *   probdoubleelidedade), which adds
+ *   probdoubleelidedade; K = 4 drops the |R| = 4 term), which adds
  *     P2[a][e][d] = p2(x_a..~x_e..~x_d..x_1)  (all of 1..a but e > d).
  *
  * Conventions for the boundary cases the update rules reach:
@@ -118,10 +118,10 @@ static double bias_k3(const Tables *t, const double *kappa, int M, const double 
     return B;
 }
 
-/* The same for K = 5 double elision, Eq. probade. The |R| = 2 term uses the
-   double-elided table p2 (the printed equation omits the symbol; the text states
-   that |R| = 1 and 2 use p1 and p2). */
-static double bias_k5(const Tables *t, const double *kappa, int M, const double *chi, int n) {
+/* The same for double elision, Eq. probade, truncated at |R| + 1 <= K (K = 4
+   or 5). The |R| = 2 term uses the double-elided table p2 (the printed equation
+   omits the symbol; the text states that |R| = 1 and 2 use p1 and p2). */
+static double bias_k5(const Tables *t, const double *kappa, int M, const double *chi, int n, int K) {
     int v[5];
     v[0] = n;
     double B = 0.5 * gam(kappa, M, chi, v, 1) * tP(t, n - 1);
@@ -140,7 +140,7 @@ static double bias_k5(const Tables *t, const double *kappa, int M, const double 
                 v[0] = i; v[1] = j; v[2] = k; v[3] = n;
                 B += 0.0625 * gam(kappa, M, chi, v, 4) * tPp(t, n - 1, i + 1) * tP2(t, i - 1, j, k);
             }
-    for (int i = 4; i <= n - 1; ++i)
+    for (int i = 4; K >= 5 && i <= n - 1; ++i)
         for (int j = 3; j <= i - 1; ++j)
             for (int k = 2; k <= j - 1; ++k)
                 for (int l = 1; l <= k - 1; ++l) {
@@ -202,7 +202,7 @@ static void update_tables(Tables *t, const double *kappa, int M, const double *c
                 }
         t->P1[n * W + e] = s;
     }
-    if (K != 5) return;
+    if (K == 3) return;
     /* p2 (x_n .. ~x_e .. ~x_d .. x_1), n-1 >= e > d >= 1 */
     for (int e = 2; e <= n - 1; ++e)
         for (int d = 1; d <= e - 1; ++d) {
@@ -219,14 +219,15 @@ static void update_tables(Tables *t, const double *kappa, int M, const double *c
         }
 }
 
-/* One sample. K = 3 (single elision) or 5 (double elision); orders = {opp, op1,
-   op2} for K = 5, each 1..3 (ignored for K = 3). u[M]: uniforms; force (may be NULL): bits to
+/* One sample. K = 3 (single elision), 4 or 5 (double elision); orders = {opp,
+   op1, op2} for K = 4, 5 (1..3, 1..3, 1..2; NULL = the defaults above; ignored
+   for K = 3). u[M]: uniforms; force (may be NULL): bits to
    score instead of drawing. Outputs (any may be NULL): bits[M], p_out = P[M],
    q0[M] = the probability of a 0 each bit was drawn with. Returns 0, or -1 on bad
    arguments or allocation failure. */
 int orc_sample(const double *kappa, int M, int K, const int *orders, const double *u, const uint8_t *force,
                uint8_t *bits, double *p_out, double *q0) {
-    if (M < K || (K != 3 && K != 5) || !kappa) return -1;
+    if (M < K || K < 3 || K > 5 || !kappa) return -1;
     if (orders && (orders[0] < 1 || orders[0] > 3 || orders[1] < 1 || orders[1] > 3 || orders[2] < 1 || orders[2] > 2))
         return -1;
     const size_t W = (size_t)M + 1;
@@ -235,19 +236,22 @@ int orc_sample(const double *kappa, int M, int K, const int *orders, const doubl
     t.P = (double *)calloc(W, sizeof(double));
     t.P1 = (double *)calloc(W * W, sizeof(double));
     t.Pp = (double *)calloc(W * W, sizeof(double));
-    t.P2 = K == 5 ? (double *)calloc(W * W * W, sizeof(double)) : NULL;
+    t.P2 = K >= 4 ? (double *)calloc(W * W * W, sizeof(double)) : NULL;
     double *chi = (double *)calloc(W, sizeof(double));
-    if (!t.P || !t.P1 || !t.Pp || (K == 5 && !t.P2) || !chi) {
+    if (!t.P || !t.P1 || !t.Pp || (K >= 4 && !t.P2) || !chi) {
         free(t.P); free(t.P1); free(t.Pp); free(t.P2); free(chi);
         return -1;
     }
-    /* K = 3: Eq. a and Eq. b are both of order 2 (there is no p2 table) */
-    const int opp = K == 3 ? 2 : (orders ? orders[0] : 3), op1 = K == 3 ? 2 : (orders ? orders[1] : 3);
-    const int op2 = orders ? orders[2] : 2;
+    /* K = 3: Eq. a and Eq. b are both of order 2 (there is no p2 table). K = 5:
+       the paper's orders 3, 3, 2. K = 4: the same rule (one order below the
+       minimum that keeps O(M^K) time) gives 2, 2, 1. */
+    const int dpp = K == 5 ? 3 : 2, dp1 = K == 5 ? 3 : 2, dp2 = K == 5 ? 2 : 1;
+    const int opp = K == 3 ? 2 : (orders ? orders[0] : dpp), op1 = K == 3 ? 2 : (orders ? orders[1] : dp1);
+    const int op2 = orders ? orders[2] : dp2;
     t.P[0] = 1.0;
     for (int n = 1; n <= M; ++n) {
         chi[n] = 1.0;
-        const double B = K == 3 ? bias_k3(&t, kappa, M, chi, n) : bias_k5(&t, kappa, M, chi, n);
+        const double B = K == 3 ? bias_k3(&t, kappa, M, chi, n) : bias_k5(&t, kappa, M, chi, n, K);
         const double p0 = 0.5 * t.P[n - 1] + B, p1 = 0.5 * t.P[n - 1] - B;
         const double c0 = p0 > 0.0 ? p0 : 0.0, c1 = p1 > 0.0 ? p1 : 0.0;
         const double qz = (c0 + c1 > 0.0) ? c0 / (c0 + c1) : 0.5;

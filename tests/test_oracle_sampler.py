@@ -3,12 +3,11 @@ the paper's expansion and by exact distributions, independent of the oracle:
 
 * Eq. probs_corr_cumulants_3 is exact when no cumulant is truncated and every
   marginal it uses is exact: the K = 3 single-elision sampler reproduces the
-  Torontonian click distribution for M <= 3, the K = 5 double-elision sampler
-  (orders 3, 3, 2) for M <= 5;
+  Torontonian click distribution for M <= 3, the double-elision sampler for
+  M <= K at K = 4 (orders 2, 2, 1) and K = 5 (orders 3, 3, 2);
 * for a state made of independent blocks of consecutive modes, every cumulant
   that spans two blocks vanishes and the approximated marginals factorise:
-  blocks of <= 3 modes (K = 3) or <= 5 modes (K = 5) give the exact product
-  distribution at any M;
+  blocks of <= K modes give the exact product distribution at any M;
 * the terms beyond the first are odd in the drawn bit, so the estimated
   probabilities of all 2^M bitstrings sum to 1;
 * drawing with seeded uniforms reproduces the exact distribution's frequencies.
@@ -63,7 +62,7 @@ def sub_table(kap, M, K, n):
     return np.concatenate(parts)
 
 
-@pytest.mark.parametrize("K", [3, 5])
+@pytest.mark.parametrize("K", [3, 4, 5])
 def test_exact_for_small_M(K):
     """M = K: nothing is truncated and every marginal the rules reach is exact."""
     inst = synthetic.random_instance(K, K, seed=300 + K, r_range=(0.5, 1.3))
@@ -72,7 +71,7 @@ def test_exact_for_small_M(K):
     np.testing.assert_allclose(p, tor_probs_of(bits, inst.V), rtol=1e-10, atol=1e-14)
 
 
-@pytest.mark.parametrize("K,sizes", [(3, (3, 2, 3, 1)), (5, (5, 2, 4))])
+@pytest.mark.parametrize("K,sizes", [(3, (3, 2, 3, 1)), (4, (4, 3, 4)), (5, (5, 2, 4))])
 def test_exact_for_independent_blocks(K, sizes):
     rng = np.random.default_rng(sum(sizes) + K)
     blocks = [synthetic.random_instance(m, 1, seed=int(rng.integers(1 << 30)), r_range=(0.5, 1.3)).V for m in sizes]
@@ -89,7 +88,7 @@ def test_exact_for_independent_blocks(K, sizes):
     np.testing.assert_allclose(p, want, rtol=1e-9)
 
 
-@pytest.mark.parametrize("K,orders", [(3, None), (5, None), (5, (2, 2, 1))])
+@pytest.mark.parametrize("K,orders", [(3, None), (4, None), (5, None), (5, (2, 2, 1))])
 def test_probabilities_sum_to_one(K, orders):
     inst = synthetic.random_instance(8, K, seed=81, r_range=(0.6, 1.4))
     bits = all_bits(8)
@@ -136,8 +135,8 @@ def test_truncation_error_is_small_for_a_lossy_state():
     bits = all_bits(8)
     exact = tor_probs_of(bits, inst.V)
     tv = {}
-    for K in (3, 5):
+    for K in (3, 4, 5):
         _, p, _ = oracle.sample(kappa_table(inst.V, K), 8, K, force=bits)
         tv[K] = 0.5 * np.abs(p - exact).sum()
     assert tv[5] < 0.02 and tv[3] < 0.05
-    assert tv[5] < tv[3]
+    assert tv[5] < tv[4] < tv[3]
