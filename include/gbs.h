@@ -177,8 +177,8 @@ typedef enum {
 } gbs_sample_precision;
 
 /* Workspace bytes for gbs_sample with this (M, K, batch, precision); 0 if invalid.
-   Grows as batch x C(M, 3) entries for K = 5 (the p2 table and the stored
-   products), batch x C(M, 2) for K = 3. */
+   Grows as batch x C(M, 3) entries for K = 4, 5 (the p2 table and, for K = 5,
+   the stored products), batch x C(M, 2) for K = 3. */
 size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);
 
 /* Chain-rule sampler (Sec. "The sampling algorithm"): draws n_samples threshold-
@@ -188,7 +188,10 @@ size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);
      K = 3: single elision (Eq. methprob, Eq. b, Eq. a);
      K = 5: double elision (Eq. probade, Eq. probpartialade, Eq. probelidedade,
             Eq. probdoubleelidedade), orders[] = expansion orders of p+, p1, p2
-            (host array, NULL = the paper's 3, 3, 2; each 1..3, 1..3, 1..2).
+            (host array, NULL = the paper's 3, 3, 2; each 1..3, 1..3, 1..2);
+     K = 4: the same without the |R| = 4 term (NULL orders = 2, 2, 1, the
+            paper's rule for K = 5 -- one order below the minimum that keeps the
+            O(M^K) time -- applied to K = 4).
    Bit n of a sample is 0 when u[s][n] < q0, q0 = max(p0, 0) / (max(p0, 0) +
    max(p1, 0)) with p0, p1 the expansion's values for the two outcomes (1/2 if
    both are <= 0). u: device [n_samples][M] uniforms in [0, 1). force (device,

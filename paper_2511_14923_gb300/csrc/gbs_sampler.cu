@@ -10,7 +10,8 @@
 // filled by truncated forms of the same rule: K = 3 single elision (Eq. methprob,
 // Eq. b, Eq. a), K = 5 double elision (Eq. probade, Eq. probpartialade,
 // Eq. probelidedade, Eq. probdoubleelidedade; orders 3, 3, 2 for p+, p1, p2 unless
-// the caller lowers them). Boundary cases: P[0] = 1, an empty p+ range is 1,
+// the caller lowers them), K = 4 the same without the |R| = 4 term (orders
+// 2, 2, 1 by default). Boundary cases: P[0] = 1, an empty p+ range is 1,
 // P1[a][a] = P[a-1], P2[a][a][d] = P1[a-1][d].
 //
 // Scaling. Each table entry over m variables is stored times 2^m. The factors
@@ -177,7 +178,7 @@ __device__ __forceinline__ void zrow(int K, int M, int t, uint64_t q, const uint
         kbase = off[3] + cb(n - 1, 3);
         kind = 3;
         dst = i_z(t, n);
-    } else {
+    } else {  // K = 5 only
         int hi, lo;
         pair_of(q - 1 - 2 * (uint64_t)(M - t), hi, lo);
         const int i = t + 1 + lo, m = t + 1 + hi;
@@ -348,7 +349,10 @@ __global__ void bias_kernel(Args<R> a, int n) {
     } else {
         for (int i = 1; i < n; ++i) B = fma(k2(a, i, n) * sp(i), p1(a, n - 1, i, s), B);
         if (n >= 3) B += a.G[s];
-        for (int i = 3; i < n; ++i) B = fma(sp(i) * pp(a, n - 1, i + 1, s), a.Y[(size_t)i * a.S + s], B);
+        // K = 5: Y = Z3 + the order-5 part (y_kernel); K = 4: Z3 alone
+        const R *Yv = K == 5 ? a.Y : nullptr;
+        for (int i = 3; i < n; ++i)
+            B = fma(sp(i) * pp(a, n - 1, i + 1, s), K == 5 ? Yv[(size_t)i * a.S + s] : a.Z[i_z(i, n) * a.S + s], B);
     }
     const R p0 = Pm + B, p1v = Pm - B;
     const R c0 = p0 > R(0) ? p0 : R(0), c1 = p1v > R(0) ? p1v : R(0);
@@ -440,7 +444,7 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
                 if (K == 3) acc = fma(g2 * pp(a, n - 1, hi + 1, s), p1(a, hi - 1, lo, s), acc);
                 else acc = fma(g2, p2(a, n - 1, hi, lo, s), acc);
             }
-        if (K == 5 && a.op1 >= 3) {
+        if (K >= 4 && a.op1 >= 3) {
             if (e >= 3) acc = fma(pp(a, n - 1, e + 1, s), a.X[i_z(e, n) * S + s], acc);
             // pairs (e, d), d < e, carry chi_d-weighted parts for e; pairs (j, e), j > e, for e
             const R *T = a.T + s;
@@ -573,15 +577,15 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.P, (size_t)M + 1);
     take(L.Pp, cb(M, 2) + (size_t)M);
     take(L.P1, cb(M, 2));
-    take(L.P2, K == 5 ? cb(M, 3) : 0);
+    take(L.P2, K >= 4 ? cb(M, 3) : 0);
     take(L.Z, cb(M, 2));
     take(L.Z5, K == 5 ? cb(M, 3) : 0);
     take(L.G, 1);
-    take(L.Y, K == 5 ? (size_t)M + 1 : 0);
-    take(L.X, K == 5 ? cb(M, 2) : 0);
-    take(L.W, K == 5 ? cb(M - 1, 2) : (size_t)M);
-    take(L.CA, K == 5 ? 3 * ((size_t)M + 1) : 0);
-    take(L.T, K == 5 ? 2 * cb(M - 1, 2) : 0);
+    take(L.Y, K >= 4 ? (size_t)M + 1 : 0);
+    take(L.X, K >= 4 ? cb(M, 2) : 0);
+    take(L.W, K >= 4 ? cb(M - 1, 2) : (size_t)M);
+    take(L.CA, K >= 4 ? 3 * ((size_t)M + 1) : 0);
+    take(L.T, K >= 4 ? 2 * cb(M - 1, 2) : 0);
     L.bw = off;
     off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
     L.kap = off;
@@ -611,19 +615,21 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
     init_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a);
     for (int t = 1; t <= M; ++t) {
         // products for this step and later ones (inputs: rows < t of the tables)
-        const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);
+        const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);  // K = 4, 5: pairs below t
         if (D > 0) {
             w_kernel<R, K><<<egrid(S, (uint64_t)D), ETB, 0, st>>>(a, t, D);
-            const uint64_t rows = K == 3 ? 1 + (uint64_t)(M - t) : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
+            const uint64_t rows = K == 3   ? 1 + (uint64_t)(M - t)
+                                  : K == 4 ? 1 + 2 * (uint64_t)(M - t)
+                                           : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
             dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
             zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
         }
         if (K == 5 && t > 3) y_kernel<R><<<egrid(S, (uint64_t)(t - 3)), ETB, 0, st>>>(a, t);
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
-        if (K == 5 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        if (K >= 4 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
-        if (K == 5 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
-        if (K == 5 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);  // before p1: fills T
+        if (K >= 4 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        if (K >= 4 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);  // before p1: fills T
         if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -642,7 +648,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.S = c.S;
     a.opp = c.K == 3 ? 2 : c.orders[0];
     a.op1 = c.K == 3 ? 2 : c.orders[1];
-    a.op2 = c.orders[2];
+    a.op2 = c.orders[2];  // the caller resolves the defaults per K
     a.off[0] = 0;
     for (int d = 1; d <= 5; ++d) a.off[d] = order_offset(c.M, d);
     a.chi = reinterpret_cast<R *>(w + L.chi);
@@ -677,8 +683,8 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
         a.force = c.force ? c.force + o : nullptr;
         a.bits = c.bits + o;
         a.q0 = c.q0 ? c.q0 + o : nullptr;
-        cudaError_t e = c.K == 3 ? run_chunk<R, 3>(a, c.prob ? c.prob + s0 : nullptr, st)
-                                 : run_chunk<R, 5>(a, c.prob ? c.prob + s0 : nullptr, st);
+        double *pr = c.prob ? c.prob + s0 : nullptr;
+        cudaError_t e = c.K == 3 ? run_chunk<R, 3>(a, pr, st) : c.K == 4 ? run_chunk<R, 4>(a, pr, st) : run_chunk<R, 5>(a, pr, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -709,7 +715,7 @@ bool dev_ptr(const void *p) {
 }
 
 bool valid_shape(int M, int K, int batch, int precision) {
-    return (K == 3 || K == 5) && M >= K && M <= GBS_MAX_MODES && batch >= 128 && batch % 128 == 0 &&
+    return K >= 3 && K <= 5 && M >= K && M <= GBS_MAX_MODES && batch >= 128 && batch % 128 == 0 &&
            (precision == GBS_SAMPLE_FP64 || precision == GBS_SAMPLE_FP32);
 }
 
@@ -728,10 +734,11 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
     using gbs::record_error;
     if (!valid_shape(M, K, batch, precision))
         return record_error(GBS_ERR_INVALID_ARG,
-                            "need K in {3, 5}, K <= M <= 1024, batch a positive multiple of 128 and precision "
+                            "need K in {3, 4, 5}, K <= M <= 1024, batch a positive multiple of 128 and precision "
                             "GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
     if (n_samples < 0) return record_error(GBS_ERR_INVALID_ARG, "n_samples must be >= 0");
-    int ord[3] = {3, 3, 2};
+    int ord[3] = {3, 3, 2};  // K = 5; K = 4: one order lower, as the paper's rule gives
+    if (K == 4) ord[0] = ord[1] = 2, ord[2] = 1;
     if (orders) {
         for (int i = 0; i < 3; ++i) ord[i] = orders[i];
         if (ord[0] < 1 || ord[0] > 3 || ord[1] < 1 || ord[1] > 3 || ord[2] < 1 || ord[2] > 2)

@@ -36,7 +36,9 @@ def uniforms(n, M, seed):
 
 @pytest.mark.parametrize("K,M,orders,n,batch", [(3, 12, None, 300, 128), (5, 14, None, 200, 128),
                                                 (5, 13, (2, 2, 1), 130, 128), (5, 9, (3, 2, 1), 64, 128),
-                                                (3, 3, None, 64, 128), (5, 5, None, 260, 128)])
+                                                (3, 3, None, 64, 128), (5, 5, None, 260, 128),
+                                                (4, 12, None, 200, 128), (4, 10, (3, 3, 2), 128, 128),
+                                                (4, 4, None, 64, 128)])
 def test_fp64_draws_match_oracle(K, M, orders, n, batch):
     inst = synthetic.random_instance(M, K, seed=500 + M + K, r_range=(0.5, 1.3))
     kap = kappa_of(inst, K)
@@ -49,7 +51,7 @@ def test_fp64_draws_match_oracle(K, M, orders, n, batch):
     assert np.abs(q0.cpu().numpy() - rq).max() <= 1e-12
 
 
-@pytest.mark.parametrize("K", [3, 5])
+@pytest.mark.parametrize("K", [3, 4, 5])
 def test_fp64_scores_all_bitstrings(K):
     M = 9
     inst = synthetic.random_instance(M, K, seed=90 + K)
@@ -62,7 +64,7 @@ def test_fp64_scores_all_bitstrings(K):
     assert abs(p.sum() - 1.0) < 1e-12
 
 
-@pytest.mark.parametrize("K,M", [(3, 24), (5, 20)])
+@pytest.mark.parametrize("K,M", [(3, 24), (4, 22), (5, 20)])
 def test_fp32_decisions_consistent_with_oracle(K, M):
     inst = synthetic.random_instance(M, K, seed=3200 + M, r_range=(0.6, 1.4), eta_range=(0.3, 0.5))
     kap = kappa_of(inst, K)
@@ -104,6 +106,6 @@ def test_invalid_arguments():
         gbs.sample(kap, 8, 5, u=u, batch=64)
     with pytest.raises(gbs.GbsError):
         gbs.sample(kap, 8, 5, u=u, orders=(4, 3, 2))
-    assert gbs.sampler_workspace_bytes(8, 4, 128) == 0
+    assert gbs.sampler_workspace_bytes(8, 6, 128) == 0
     assert gbs.sampler_workspace_bytes(4, 5, 128) == 0
     assert gbs.sampler_workspace_bytes(8, 5, 64) == 0
