@@ -45,7 +45,7 @@ DTYPE = {"fp64": "f64", "fp32r": "f32 determinant steps refined to f64 accuracy;
 # DRAM bytes (read + write) per launch of the order-5 kernel at M=144 under the
 # tuned schedules, from the ncu launch list in profiles/launches_m144k5_tuned.md.
 # Reset to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES = {"fp32r": 6.6275e9 + 4.2786e9, "fp64": 2.9781e9 + 4.2348e9}
+TRAFFIC_BYTES = {"fp32r": 6.2201e9 + 4.2769e9, "fp64": 3.1267e9 + 4.2348e9}
 FP64_FMA_PER_CLK_PER_SM = 2  # nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz
 
 
