@@ -408,12 +408,12 @@ def bench_sampler(args):
     with ClockSampler() as clk:
         for k, (a, b) in enumerate(ev):
             a.record()
-            bits, prob, _ = gbs.sample(kap, M, K, u=us[warm + k], batch=B, precision="fp32", workspace=ws,
+            bits, logp, _ = gbs.sample(kap, M, K, u=us[warm + k], batch=B, precision="fp32", workspace=ws,
                                        check=False)
             b.record()
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-    ok = bool(torch.isfinite(prob).all())
+    ok = bool(torch.isfinite(logp).all())
     # end to end: uniforms from pinned host memory in, bitstrings out, every step
     uh = us[0].cpu().pin_memory()
     bh = torch.empty((B, M), dtype=torch.uint8).pin_memory()

@@ -70,11 +70,17 @@ typedef enum {
 
 #define GBS_MAX_ORDER 5
 #define GBS_MAX_MODES 1024
+/* Tables with kmax <= 3 (and the K = 3 sampler) never use the prefix-tree
+   kernels and accept up to this many modes, e.g. the 1152-mode state of a
+   144-mode interferometer read out through 8 time bins (Sec. "High-brightness
+   results for Jiuzhang 3.0"). */
+#define GBS_MAX_MODES_K3 4096
 
 /* ---------------------------------------------------------------- host helpers */
 
 /* Number of table entries: sum_{d=1..kmax} C(M, d); 0 if the arguments are invalid
-   (M < 1, M > GBS_MAX_MODES, kmax < 1, kmax > min(M, GBS_MAX_ORDER)). */
+   (M < 1, kmax < 1, kmax > min(M, GBS_MAX_ORDER), M > GBS_MAX_MODES for kmax >= 4,
+   M > GBS_MAX_MODES_K3 for kmax <= 3). */
 uint64_t gbs_table_size(int M, int kmax);
 
 /* First entry of the order-d group: sum_{e<d} C(M, e), e >= 1. 0 for invalid d. */
@@ -82,7 +88,7 @@ uint64_t gbs_order_offset(int M, int d);
 
 /* Colex rank of a sorted mode set modes[0] < ... < modes[d-1]: sum C(modes[i], i+1).
    Returns UINT64_MAX if modes is NULL, d is out of [1, GBS_MAX_ORDER] or the
-   modes are not strictly increasing and non-negative. */
+   modes are not strictly increasing in [0, GBS_MAX_MODES_K3). */
 uint64_t gbs_rank(const int *modes, int d);
 
 /* Inverse of gbs_rank: writes the d sorted modes of rank r to modes_out.
@@ -196,13 +202,16 @@ size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);
    max(p1, 0)) with p0, p1 the expansion's values for the two outcomes (1/2 if
    both are <= 0). u: device [n_samples][M] uniforms in [0, 1). force (device,
    may be NULL): [n_samples][M] bits to score instead of drawing; u is then
-   ignored. Outputs (device): bits_out [n_samples][M]; prob_out [n_samples]
-   (may be NULL) = the estimated probability of each bitstring; q0_out
-   [n_samples][M] (may be NULL). Samples run in chunks of batch (a multiple of
+   ignored. Outputs (device): bits_out [n_samples][M]; logp_out [n_samples]
+   (may be NULL) = the natural log of the estimated probability of each
+   bitstring (NaN if the estimate is <= 0); q0_out [n_samples][M] (may be
+   NULL). Internally every table entry is kept multiplied by prod_v exp(H_v)
+   over its variables, H_v the click entropy of mode v, which keeps the values
+   of long bitstrings inside the FP32 / FP64 range. Samples run in chunks of batch (a multiple of
    128) sharing one workspace of gbs_sampler_workspace_bytes(M, K, batch,
    precision) bytes. Asynchronous on cuda_stream. */
 int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_samples, const double *u,
-               const uint8_t *force, uint8_t *bits_out, double *prob_out, double *q0_out, int batch, int precision,
+               const uint8_t *force, uint8_t *bits_out, double *logp_out, double *q0_out, int batch, int precision,
                void *workspace, size_t ws_bytes, void *cuda_stream);
 
 /* ---------------------------------------------------------------- schedule autotuning */
@@ -260,7 +269,7 @@ int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream);
 
 /* Workspace bytes for gbs_cumulants_backward (includes the P0, inverse-moment and
    P0-gradient tables, 3 x 8 B x gbs_table_size, plus the forward workspace);
-   0 if the arguments are invalid. */
+   0 if the arguments are invalid. The adjoint takes M <= GBS_MAX_MODES. */
 size_t gbs_backward_workspace_bytes(int M, int kmax);
 
 /* Adjoint of gbs_cumulants (FP64). grad_kappa[gbs_table_size(M,kmax)] = dL/dkt(S)

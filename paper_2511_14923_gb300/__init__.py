@@ -229,8 +229,9 @@ def sample(kappa, M: int, K: int, u=None, force=None, orders=None, batch: int = 
            want_q0: bool = False, workspace=None, check: bool = True):
     """Chain-rule sampler (gbs_sample): bitstrings drawn from the spin-cumulant table
     kappa (CUDA float64, orders 1..K). u: (n, M) CUDA float64 uniforms, or force:
-    (n, M) CUDA uint8 bits to score. Returns (bits (n, M) uint8, prob (n,) float64,
-    q0 (n, M) float64 or None)."""
+    (n, M) CUDA uint8 bits to score. Returns (bits (n, M) uint8, logp (n,) float64 =
+    natural log of each bitstring's estimated probability, q0 (n, M) float64 or
+    None)."""
     kappa = _dev64(kappa, "kappa")
     if kappa.numel() != table_size(M, K):
         raise ValueError(f"kappa must hold table_size(M, K) = {table_size(M, K)} entries")

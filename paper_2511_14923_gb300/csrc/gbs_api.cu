@@ -34,8 +34,12 @@ int ok() {
     return GBS_OK;
 }
 
+// Orders 4 and 5 run the prefix-tree kernels (shared-memory x-entries sized for
+// GBS_MAX_MODES); orders 1-3 run one thread per subset and take larger M.
+int max_modes(int kmax) { return kmax <= 3 ? GBS_MAX_MODES_K3 : GBS_MAX_MODES; }
+
 bool valid_mk(int M, int kmax) {
-    return M >= 1 && M <= GBS_MAX_MODES && kmax >= 1 && kmax <= GBS_MAX_ORDER && kmax <= M;
+    return M >= 1 && kmax >= 1 && kmax <= GBS_MAX_ORDER && kmax <= M && M <= max_modes(kmax);
 }
 
 int device_sms() {
@@ -58,8 +62,9 @@ bool is_device_ptr(const void *p) {
 int check_common(const double *V, int M, int kmax, const void *out, int precision, void *ws, size_t ws_bytes,
                  gbs::WsLayout &L, int &sms) {
     if (!valid_mk(M, kmax))
-        return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d and 1 <= kmax <= min(M, %d); got M=%d kmax=%d",
-                    GBS_MAX_MODES, GBS_MAX_ORDER, M, kmax);
+        return fail(GBS_ERR_INVALID_ARG,
+                    "need 1 <= kmax <= min(M, %d) and M <= %d (kmax >= 4) or %d (kmax <= 3); got M=%d kmax=%d",
+                    GBS_MAX_ORDER, GBS_MAX_MODES, GBS_MAX_MODES_K3, M, kmax);
     if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
         return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
     if (!V || !out || !ws) return fail(GBS_ERR_INVALID_ARG, "V, output and workspace must be non-NULL");
@@ -141,7 +146,7 @@ uint64_t gbs_table_size(int M, int kmax) {
 }
 
 uint64_t gbs_order_offset(int M, int d) {
-    if (M < 1 || M > GBS_MAX_MODES || d < 1 || d > GBS_MAX_ORDER || d > M) return 0;
+    if (M < 1 || M > GBS_MAX_MODES_K3 || d < 1 || d > GBS_MAX_ORDER || d > M) return 0;
     return gbs::order_offset(M, d);
 }
 
@@ -149,7 +154,7 @@ uint64_t gbs_rank(const int *modes, int d) {
     if (!modes || d < 1 || d > GBS_MAX_ORDER) return UINT64_MAX;
     uint64_t r = 0;
     for (int i = 0; i < d; ++i) {
-        if (modes[i] < 0 || modes[i] >= GBS_MAX_MODES || (i > 0 && modes[i] <= modes[i - 1])) return UINT64_MAX;
+        if (modes[i] < 0 || modes[i] >= GBS_MAX_MODES_K3 || (i > 0 && modes[i] <= modes[i - 1])) return UINT64_MAX;
         r += gbs::binom(modes[i], i + 1);
     }
     return r;
@@ -157,10 +162,10 @@ uint64_t gbs_rank(const int *modes, int d) {
 
 int gbs_unrank(uint64_t r, int d, int *modes_out) {
     if (!modes_out || d < 1 || d > GBS_MAX_ORDER) return fail(GBS_ERR_INVALID_ARG, "bad d or NULL output");
-    if (r >= gbs::binom(GBS_MAX_MODES, d)) return fail(GBS_ERR_INVALID_ARG, "rank out of range");
+    if (r >= gbs::binom(GBS_MAX_MODES_K3, d)) return fail(GBS_ERR_INVALID_ARG, "rank out of range");
     for (int k = d; k >= 1; --k) {
-        // largest c with C(c, k) <= r, by bisection over [k-1, GBS_MAX_MODES)
-        int lo = k - 1, hi = GBS_MAX_MODES;
+        // largest c with C(c, k) <= r, by bisection over [k-1, GBS_MAX_MODES_K3)
+        int lo = k - 1, hi = GBS_MAX_MODES_K3;
         while (hi - lo > 1) {
             const int mid = (lo + hi) / 2;
             if (gbs::binom(mid, k) <= r) lo = mid;
@@ -215,14 +220,14 @@ int gbs_stream_status(const void *workspace, void *cuda_stream) {
 }
 
 size_t gbs_backward_workspace_bytes(int M, int kmax) {
-    if (!valid_mk(M, kmax)) return 0;
+    if (!valid_mk(M, kmax) || M > GBS_MAX_MODES) return 0;
     const int sms = device_sms();
     return gbs::bwd_layout(M, kmax, sms > 0 ? sms : 1).total;
 }
 
 int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_kappa, double *grad_V,
                            void *workspace, size_t ws_bytes, void *cuda_stream) {
-    if (!valid_mk(M, kmax))
+    if (!valid_mk(M, kmax) || M > GBS_MAX_MODES)
         return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d and 1 <= kmax <= min(M, %d); got M=%d kmax=%d",
                     GBS_MAX_MODES, GBS_MAX_ORDER, M, kmax);
     if (!V || !grad_kappa || !grad_V || !workspace)
@@ -274,7 +279,7 @@ static int check_batch(const gbs_instance *inst, int n, int precision) {
     if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
         return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
     for (int i = 0; i < n; ++i) {
-        if (!valid_mk(inst[i].M, inst[i].kmax))
+        if (!valid_mk(inst[i].M, inst[i].kmax) || inst[i].M > GBS_MAX_MODES)
             return fail(GBS_ERR_INVALID_ARG, "instance %d: need 1 <= M <= %d and 1 <= kmax <= min(M, %d)", i,
                         GBS_MAX_MODES, GBS_MAX_ORDER);
         if (!inst[i].V || !inst[i].kappa_out || ((uintptr_t)inst[i].V & 7) || ((uintptr_t)inst[i].kappa_out & 7))
@@ -324,7 +329,7 @@ int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream) {
 
 int gbs_covariance(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
                    double *V_out, void *cuda_stream) {
-    if (M < 1 || M > GBS_MAX_MODES) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES);
+    if (M < 1 || M > GBS_MAX_MODES_K3) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES_K3);
     const void *ptrs[] = {U_re, U_im, r, eta, V_out};
     for (const void *p : ptrs)
         if (!p || ((uintptr_t)p & 7) || !is_device_ptr(p))
@@ -337,7 +342,7 @@ int gbs_covariance(const double *U_re, const double *U_im, const double *r, cons
 int gbs_covariance_backward(const double *U_re, const double *U_im, const double *r, const double *eta, int M,
                             const double *V, const double *grad_V, double *grad_r, double *grad_eta,
                             void *cuda_stream) {
-    if (M < 1 || M > GBS_MAX_MODES) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES);
+    if (M < 1 || M > GBS_MAX_MODES_K3) return fail(GBS_ERR_INVALID_ARG, "need 1 <= M <= %d", GBS_MAX_MODES_K3);
     const void *ptrs[] = {U_re, U_im, r, eta, V, grad_V, grad_r, grad_eta};
     for (const void *p : ptrs)
         if (!p || ((uintptr_t)p & 7) || !is_device_ptr(p))

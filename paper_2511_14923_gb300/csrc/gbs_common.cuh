@@ -15,9 +15,10 @@ enum : unsigned {
 };
 
 // ---------------------------------------------------------------- combinatorics
-// C(n, k) for 0 <= k <= 6 and 0 <= n <= 1030 (n^6 < 2^64); 0 if n < k or k < 0.
-// Each step r <- r (n - i) / (i + 1) keeps r = C(n, i + 1) exact, and the
-// divisors are constants, so no runtime 64-bit division is emitted.
+// C(n, k) for 0 <= k <= 6; 0 if n < k or k < 0. Each step r <- r (n - i) / (i + 1)
+// keeps r = C(n, i + 1) exact, and the divisors are constants, so no runtime
+// 64-bit division is emitted. The largest intermediate, C(n, k-1) (n - k + 1),
+// stays below 2^64 for k <= 5 up to n = 4096 and for k = 6 up to n = 1030.
 __host__ __device__ __forceinline__ uint64_t binom(int n, int k) {
     if (n < k || k < 0) return 0;
     const uint64_t N = (uint64_t)n;

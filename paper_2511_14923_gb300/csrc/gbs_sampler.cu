@@ -14,10 +14,16 @@
 // 2, 2, 1 by default). Boundary cases: P[0] = 1, an empty p+ range is 1,
 // P1[a][a] = P[a-1], P2[a][a][d] = P1[a-1][d].
 //
-// Scaling. Each table entry over m variables is stored times 2^m. The factors
-// 1/2, 1/4, ... of the rule then cancel exactly (every term of a sum covers the
-// same number of variables), the stored values stay near 1 instead of 2^-M, and
-// p(x_n = 0) = (P~[n-1] + B~) / 2^n, p(x_n = 1) = (P~[n-1] - B~) / 2^n.
+// Scaling. Each table entry over a variable set A is stored times prod_{v in A}
+// s_v, with s_v = exp(H_v) and H_v the click entropy of mode v - 1 (from
+// kappa({v})), so that a typical sample's values stay near 1 instead of
+// decaying like e^{-sum H}. Writing hs_v = s_v / 2 and kappa'(S) = kappa(S)
+// prod_{v in S} hs_v, every rule keeps its form with the factors 2^{-(|R|+1)}
+// absorbed: the term of R becomes chi kappa'(R + {n}) times the scaled
+// marginal, and the leading 1/2 (1 + gamma_n) becomes hs_n + chi_n kappa'_n.
+// Then p(x_n = 0) and p(x_n = 1) are proportional to hs_n P~[n-1] +- B~, with B~
+// the scaled odd part, and the probability of a bitstring is
+// P~[M] exp(-sum_v H_v).
 //
 // Factorisation of the expensive terms. The terms of the bias B that reach back
 // to a table row j - 1 through P2[j-1] (or P1[j-1] for K = 3) are sums over
@@ -34,10 +40,11 @@
 // whose largest index is the elided one);
 // (K = 3) the order-2 set {., j} and the order-3 sets {., j, n}. At step n the
 // bias then only combines stored Z values with p+ factors:
-//   K = 5: B~ = kappa_n P~[n-1] + sum_i kappa(i,n) chi_i P1~[n-1][i] + G3
+//   K = 5: B~ = kappa'_n P~[n-1] + sum_i kappa'(i,n) chi_i P1~[n-1][i] + G3
 //             + sum_{i<n} chi_i Pp~[n-1][i+1] (Z3_i(n) + sum_{j<i} chi_j Pp~[i-1][j+1] Z5_j(i,n))
-//   K = 3: B~ = kappa_n P~[n-1] + G2 + sum_{i<n} chi_i Pp~[n-1][i+1] Z_i(n)
-// (chi_n taken as +1: every term but P~[n-1] is odd in x_n).
+//   K = 3: B~ = kappa'_n P~[n-1] + G2 + sum_{i<n} chi_i Pp~[n-1][i+1] Z_i(n)
+// (chi_n taken as +1: every term but hs_n P~[n-1] is odd in x_n; kappa' in every
+// product row).
 //
 // Drawing. x_n = 0 when u_n < q0 = max(p0, 0) / (max(p0, 0) + max(p1, 0))
 // (1/2 if both are <= 0); P[n] keeps the chosen branch unclipped.
@@ -76,6 +83,8 @@ struct Args {
     R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X, *W;
     R *CA, *CB, *CC;       // per-step coefficients [i][S]: chi_i Pp~[n-1][i+1], kappa(i,n) chi_i, kappa(i,n) chi_i Pp~[n-1][i+1]
     R *T;                  // [C(M,2)][2][S] per-pair parts of the p1 order-3 term (see p2_kernel)
+    const R *hs;           // per-variable half scale s_v / 2, hs[v], v = 1..M
+    const double *H;       // per-variable log scale ln s_v (the click entropy of mode v - 1)
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -354,7 +363,7 @@ __global__ void bias_kernel(Args<R> a, int n) {
         for (int i = 3; i < n; ++i)
             B = fma(sp(i) * pp(a, n - 1, i + 1, s), K == 5 ? Yv[(size_t)i * a.S + s] : a.Z[i_z(i, n) * a.S + s], B);
     }
-    const R p0 = Pm + B, p1v = Pm - B;
+    const R p0 = fma(a.hs[n], Pm, B), p1v = fma(a.hs[n], Pm, -B);
     const R c0 = p0 > R(0) ? p0 : R(0), c1 = p1v > R(0) ? p1v : R(0);
     const R q = (c0 + c1 > R(0)) ? c0 / (c0 + c1) : R(0.5);
     int x = 0;
@@ -405,7 +414,7 @@ __global__ void __launch_bounds__(ETB) pp_kernel(Args<R> a, int n) {
                 acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), acc);
         if (a.opp >= 3)
             for (int j = l; j < n - 1; ++j) acc = fma(a.Y[(size_t)j * a.S + s], pp(a, j - 1, l, s), acc);
-        a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * pp(a, n - 1, l, s));
+        a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * pp(a, n - 1, l, s));
     }
 }
 
@@ -452,7 +461,7 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
             for (int d = 1; d < e; ++d) acc = fma(sd(d), T[(2 * (cb(e - 1, 2) + (uint64_t)(d - 1))) * S], acc);
             for (int j = e + 1; j < n; ++j) acc = fma(sd(j), T[(2 * (cb(j - 1, 2) + (uint64_t)(e - 1)) + 1) * S], acc);
         }
-        a.P1[i_p1(n, e) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p1(a, n - 1, e, s));
+        a.P1[i_p1(n, e) * S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * p1(a, n - 1, e, s));
     }
 }
 
@@ -535,7 +544,7 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
             a.T[o * S + s] = tE;
             a.T[(o + 1) * S + s] = tD;
         }
-        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, (R(1) + k1(a, n) * cn) * p2(a, n - 1, e, d, s));
+        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * p2(a, n - 1, e, d, s));
     }
 }
 
@@ -549,15 +558,56 @@ __global__ void init_kernel(Args<R> a) {
     }
 }
 
+// ln of the estimated probability: ln P~[M] - sum_v ln s_v (NaN if P~[M] <= 0).
 template <class R>
-__global__ void prob_kernel(Args<R> a, double *prob) {
+__global__ void logp_kernel(Args<R> a, double *logp) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < a.n_valid) prob[s] = ldexp((double)a.P[(size_t)a.M * a.S + s], -a.M);
+    if (s >= a.n_valid) return;
+    double h = 0.0;
+    for (int v = 1; v <= a.M; ++v) h += a.H[v];
+    const double P = (double)a.P[(size_t)a.M * a.S + s];
+    logp[s] = P > 0.0 ? log(P) - h : __longlong_as_double(0x7ff8000000000000ULL);
 }
 
-__global__ void convert_kernel(const double *__restrict__ in, float *__restrict__ out, uint64_t n) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
+// Per-variable scales from the order-1 cumulants: kappa({v}) = c_v = <(-1)^{x_v}>,
+// so mode v - 1 is silent with probability (1 + c_v) / 2; s_v = exp(H_v) with H_v
+// that binary entropy in nats (s_v in [1, 2]).
+template <class R>
+__global__ void scale_kernel(const double *__restrict__ kap, int M, R *hs, double *H) {
+    const int v = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > M) return;
+    double p0 = 0.5 * (1.0 + kap[v - 1]);
+    p0 = p0 < 0.0 ? 0.0 : (p0 > 1.0 ? 1.0 : p0);
+    const double p1 = 1.0 - p0;
+    const double h = (p0 > 0.0 ? -p0 * log(p0) : 0.0) + (p1 > 0.0 ? -p1 * log(p1) : 0.0);
+    H[v] = h;
+    hs[v] = (R)(0.5 * exp(h));
+}
+
+// kappa'(S) = kappa(S) prod_{v in S} s_v / 2 for every table entry, in the
+// arithmetic precision R. A thread takes KS_CHUNK consecutive entries of one
+// order: it unranks the first and steps through the rest by colex successor.
+constexpr int KS_CHUNK = 64;
+
+template <class R>
+__global__ void kscale_kernel(const double *__restrict__ kap, int M, int d, uint64_t off, uint64_t n,
+                              const R *__restrict__ hs, R *__restrict__ out) {
+    const uint64_t r0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * KS_CHUNK;
+    if (r0 >= n) return;
+    const uint64_t r1 = r0 + KS_CHUNK < n ? r0 + KS_CHUNK : n;
+    int c[6];
+    colex_unrank(r0, d, c);
+    c[d] = M;  // sentinel
+    for (uint64_t r = r0; r < r1; ++r) {
+        double f = 1.0;
+        for (int i = 0; i < d; ++i) f *= (double)hs[c[i] + 1];
+        out[off + r] = (R)(kap[off + r] * f);
+        // successor: the first element that can move up moves up, the ones below reset
+        int i = 0;
+        while (i < d - 1 && c[i] + 1 == c[i + 1]) ++i;
+        ++c[i];
+        for (int j = 0; j < i; ++j) c[j] = j;
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -588,10 +638,14 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.T, K >= 4 ? 2 * cb(M - 1, 2) : 0);
     L.bw = off;
     off = a256(off + (size_t)(M / 32 + 1) * Ss * sizeof(uint32_t));
-    L.kap = off;
+    L.kap = off;  // the rescaled cumulants kappa', in the arithmetic precision
     uint64_t nk = 0;
     for (int d = 1; d <= K; ++d) nk += cb(M, d);
-    if (precision != 0) off = a256(off + nk * sizeof(float));
+    off = a256(off + nk * es);
+    L.hs = off;
+    off = a256(off + ((size_t)M + 1) * es);
+    L.H = off;
+    off = a256(off + ((size_t)M + 1) * sizeof(double));
     L.total = off;
     return L;
 }
@@ -634,7 +688,7 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (prob) prob_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a, prob);
+    if (prob) logp_kernel<R><<<(S + TB - 1) / TB, TB, 0, st>>>(a, prob);
     return cudaGetLastError();
 }
 
@@ -667,14 +721,20 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.CC = a.CB + ((size_t)c.M + 1) * c.S;
     a.T = reinterpret_cast<R *>(w + L.T);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
-    if (sizeof(R) == sizeof(double)) {
-        a.kap = reinterpret_cast<const R *>(c.kappa);
-    } else {
-        uint64_t nk = 0;
-        for (int d = 1; d <= c.K; ++d) nk += cb(c.M, d);
-        float *kf = reinterpret_cast<float *>(w + L.kap);
-        convert_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(c.kappa, kf, nk);
-        a.kap = reinterpret_cast<const R *>(kf);
+    {
+        R *hs = reinterpret_cast<R *>(w + L.hs);
+        double *H = reinterpret_cast<double *>(w + L.H);
+        R *kf = reinterpret_cast<R *>(w + L.kap);
+        scale_kernel<R><<<(c.M + 255) / 256, 256, 0, st>>>(c.kappa, c.M, hs, H);
+        uint64_t off = 0;
+        for (int d = 1; d <= c.K; ++d) {
+            const uint64_t n = cb(c.M, d), threads = (n + KS_CHUNK - 1) / KS_CHUNK;
+            kscale_kernel<R><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(c.kappa, c.M, d, off, n, hs, kf);
+            off += n;
+        }
+        a.kap = kf;
+        a.hs = hs;
+        a.H = H;
     }
     for (int s0 = 0; s0 < c.n_samples; s0 += c.S) {
         a.n_valid = c.n_samples - s0 < c.S ? c.n_samples - s0 : c.S;
@@ -715,7 +775,8 @@ bool dev_ptr(const void *p) {
 }
 
 bool valid_shape(int M, int K, int batch, int precision) {
-    return K >= 3 && K <= 5 && M >= K && M <= GBS_MAX_MODES && batch >= 128 && batch % 128 == 0 &&
+    return K >= 3 && K <= 5 && M >= K && M <= (K == 3 ? GBS_MAX_MODES_K3 : GBS_MAX_MODES) && batch >= 128 &&
+           batch % 128 == 0 &&
            (precision == GBS_SAMPLE_FP64 || precision == GBS_SAMPLE_FP32);
 }
 
@@ -729,12 +790,12 @@ size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision) {
 }
 
 int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_samples, const double *u,
-               const uint8_t *force, uint8_t *bits_out, double *prob_out, double *q0_out, int batch, int precision,
+               const uint8_t *force, uint8_t *bits_out, double *logp_out, double *q0_out, int batch, int precision,
                void *workspace, size_t ws_bytes, void *cuda_stream) {
     using gbs::record_error;
     if (!valid_shape(M, K, batch, precision))
         return record_error(GBS_ERR_INVALID_ARG,
-                            "need K in {3, 4, 5}, K <= M <= 1024, batch a positive multiple of 128 and precision "
+                            "need K in {3, 4, 5}, K <= M <= 1024 (4096 for K = 3), batch a positive multiple of 128 and precision "
                             "GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
     if (n_samples < 0) return record_error(GBS_ERR_INVALID_ARG, "n_samples must be >= 0");
     int ord[3] = {3, 3, 2};  // K = 5; K = 4: one order lower, as the paper's rule gives
@@ -746,11 +807,11 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
     }
     if (!kappa || !bits_out || !workspace || (!u && !force))
         return record_error(GBS_ERR_INVALID_ARG, "kappa, bits_out, workspace and one of u / force must be non-NULL");
-    if (((uintptr_t)kappa & 7) || (u && ((uintptr_t)u & 7)) || (prob_out && ((uintptr_t)prob_out & 7)) ||
+    if (((uintptr_t)kappa & 7) || (u && ((uintptr_t)u & 7)) || (logp_out && ((uintptr_t)logp_out & 7)) ||
         (q0_out && ((uintptr_t)q0_out & 7)) || ((uintptr_t)workspace & 255))
         return record_error(GBS_ERR_INVALID_ARG, "double arrays must be 8-byte aligned, the workspace 256-byte aligned");
     if (!dev_ptr(kappa) || !dev_ptr(bits_out) || !dev_ptr(workspace) || (u && !dev_ptr(u)) ||
-        (force && !dev_ptr(force)) || (prob_out && !dev_ptr(prob_out)) || (q0_out && !dev_ptr(q0_out)))
+        (force && !dev_ptr(force)) || (logp_out && !dev_ptr(logp_out)) || (q0_out && !dev_ptr(q0_out)))
         return record_error(GBS_ERR_INVALID_ARG, "all arrays must be CUDA device (or managed) memory");
     const gbs::smp::SamplerLayout L = gbs::smp::sampler_layout(M, K, batch, precision);
     if (ws_bytes < L.total) return record_error(GBS_ERR_WORKSPACE, "workspace smaller than gbs_sampler_workspace_bytes()");
@@ -766,7 +827,7 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
     c.u = u;
     c.force = force;
     c.bits = bits_out;
-    c.prob = prob_out;
+    c.prob = logp_out;
     c.q0 = q0_out;
     c.ws = workspace;
     cudaError_t e = gbs::smp::launch_sampler(c, static_cast<cudaStream_t>(cuda_stream));

@@ -9,7 +9,7 @@ namespace smp {
 
 // Byte offsets of the per-sample arrays ([entries][S]) in the workspace.
 struct SamplerLayout {
-    size_t chi, P, Pp, P1, P2, Z, Z5, G, Y, X, W, CA, T, bw, kap, total;
+    size_t chi, P, Pp, P1, P2, Z, Z5, G, Y, X, W, CA, T, bw, kap, hs, H, total;
 };
 SamplerLayout sampler_layout(int M, int K, int S, int precision);
 
@@ -20,7 +20,7 @@ struct SamplerCall {
     const double *u;       // [n_samples][M] uniforms, or null when force is given
     const uint8_t *force;  // [n_samples][M] bits to score, or null
     uint8_t *bits;         // [n_samples][M]
-    double *prob;          // [n_samples] or null
+    double *prob;          // [n_samples] ln of the estimated probability, or null
     double *q0;            // [n_samples][M] or null
     void *ws;
 };

@@ -41,7 +41,7 @@ def test_table_size_and_offsets():
             assert gbs.order_offset(M, k) == sum(comb(M, d) for d in range(1, k))
     assert gbs.table_size(144, 5) == 498685188
     assert gbs.table_size(0, 1) == 0 and gbs.table_size(4, 5) == 0 and gbs.table_size(10, 6) == 0
-    assert gbs.table_size(1025, 1) == 0
+    assert gbs.table_size(4097, 1) == 0 and gbs.table_size(1025, 4) == 0
 
 
 @pytest.mark.parametrize("M", [1, 6, 11, 20])
@@ -67,7 +67,7 @@ def test_rank_rejects_bad_input():
     assert gbs.rank([4, 2]) == 2**64 - 1
     assert gbs.rank([-1]) == 2**64 - 1
     with pytest.raises(gbs.GbsError):
-        gbs.unrank(comb(1024, 2), 2)
+        gbs.unrank(comb(4096, 2), 2)
 
 
 def test_workspace_bytes_rejects_invalid():
@@ -84,3 +84,21 @@ def test_compute_entry_rejects_bad_arguments_without_launching():
     assert L.gbs_cumulants(vp(0), 8, 9, vp(0), 0, vp(0), 0, vp(0)) == 1
     assert L.gbs_vacuum_probs(vp(0), 8, 3, vp(0), 5, vp(0), 0, vp(0)) == 1
     assert b"kmax" in L.gbs_last_error() or b"precision" in L.gbs_last_error()
+
+
+def test_large_mode_counts_for_low_orders():
+    """kmax <= 3 (and the K = 3 sampler) accept up to 4096 modes; kmax >= 4 stays
+    at 1024. Ranks of mode sets up to 4095 are exact."""
+    assert gbs.table_size(4096, 3) == comb(4096, 1) + comb(4096, 2) + comb(4096, 3)
+    assert gbs.table_size(1152, 3) == 1152 + comb(1152, 2) + comb(1152, 3)
+    assert gbs.table_size(4097, 3) == 0 and gbs.table_size(1025, 4) == 0 and gbs.table_size(1024, 4) > 0
+    assert gbs.order_offset(4096, 3) == 4096 + comb(4096, 2)
+    rng = np.random.default_rng(4)
+    for _ in range(300):
+        d = int(rng.integers(1, 6))
+        S = np.sort(rng.choice(4096, d, replace=False))
+        r = gbs.rank(S)
+        assert r == sum(comb(int(c), i + 1) for i, c in enumerate(S))
+        assert gbs.unrank(r, d) == [int(c) for c in S]
+    assert gbs.rank([4096]) == 2 ** 64 - 1
+    assert gbs.lib().gbs_backward_workspace_bytes(1152, 3) == 0

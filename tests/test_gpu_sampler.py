@@ -2,12 +2,12 @@
 on the same seeded uniforms.
 
 FP64: the kernels sum in another order than the oracle, so probabilities agree
-to rounding (relative 1e-11 here) and every drawn bit is the oracle's (a
+to rounding (log-probabilities within 1e-11) and every drawn bit is the oracle's (a
 decision could only differ when u falls within ~1e-13 of q0). FP32 (the
 precision the paper stores its tables in): each GPU decision is checked against
 the oracle's q0 for the GPU's own bitstring (scored with forced bits) -- a bit
 may differ from u < q0 only when |u - q0| < 2e-4 -- and the GPU's q0 and
-probability agree with the oracle's within 2e-4 absolute and 1e-3 relative,
+log-probability agree with the oracle's within 2e-4 and 1e-3 absolute,
 a bound from the FP32 unit roundoff (6e-8) times the few thousand terms of the
 longest sums at these sizes."""
 import numpy as np
@@ -43,11 +43,11 @@ def test_fp64_draws_match_oracle(K, M, orders, n, batch):
     inst = synthetic.random_instance(M, K, seed=500 + M + K, r_range=(0.5, 1.3))
     kap = kappa_of(inst, K)
     u = uniforms(n, M, seed=M * 7 + K)
-    bits, prob, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), orders=orders, batch=batch,
+    bits, logp, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), orders=orders, batch=batch,
                                 precision="fp64", want_q0=True)
     rb, rp, rq = oracle.sample(kap.cpu().numpy(), M, K, u=u, orders=orders)
     assert np.array_equal(bits.cpu().numpy(), rb)
-    np.testing.assert_allclose(prob.cpu().numpy(), rp, rtol=1e-11)
+    np.testing.assert_allclose(logp.cpu().numpy(), np.log(rp), rtol=0, atol=1e-11)
     assert np.abs(q0.cpu().numpy() - rq).max() <= 1e-12
 
 
@@ -57,9 +57,9 @@ def test_fp64_scores_all_bitstrings(K):
     inst = synthetic.random_instance(M, K, seed=90 + K)
     kap = kappa_of(inst, K)
     allb = ((np.arange(1 << M)[:, None] >> np.arange(M)) & 1).astype(np.uint8)
-    _, prob, _ = gbs.sample(kap, M, K, force=torch.from_numpy(allb).cuda(), batch=128, precision="fp64")
+    _, logp, _ = gbs.sample(kap, M, K, force=torch.from_numpy(allb).cuda(), batch=128, precision="fp64")
     _, rp, _ = oracle.sample(kap.cpu().numpy(), M, K, force=allb)
-    p = prob.cpu().numpy()
+    p = np.exp(logp.cpu().numpy())
     np.testing.assert_allclose(p, rp, rtol=1e-11, atol=1e-17)
     assert abs(p.sum() - 1.0) < 1e-12
 
@@ -70,13 +70,13 @@ def test_fp32_decisions_consistent_with_oracle(K, M):
     kap = kappa_of(inst, K)
     n = 256
     u = uniforms(n, M, seed=11)
-    bits, prob, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+    bits, logp, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
                                 want_q0=True)
     b = bits.cpu().numpy()
     _, rp, rq = oracle.sample(kap.cpu().numpy(), M, K, force=b)
     tau = 2e-4
     assert np.abs(q0.cpu().numpy() - rq).max() <= tau
-    np.testing.assert_allclose(prob.cpu().numpy(), rp, rtol=1e-3)
+    np.testing.assert_allclose(logp.cpu().numpy(), np.log(rp), rtol=0, atol=1e-3)
     drawn_zero = b == 0
     assert np.all(np.where(drawn_zero, u < rq + tau, u >= rq - tau))
 
@@ -87,15 +87,34 @@ def test_fp32_m144_k5_consistent_on_a_few_samples():
     kap = kappa_of(inst, 5)
     n = 64
     u = uniforms(n, 144, seed=144)
-    bits, prob, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+    bits, logp, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
                                 want_q0=True)
-    assert bool(torch.isfinite(prob).all()) and bool((prob > 0).all())
+    assert bool(torch.isfinite(logp).all())
     b = bits.cpu().numpy()[:2]
     _, rp, rq = oracle.sample(kap.cpu().numpy(), 144, 5, force=b)
     tau = 2e-4
     assert np.abs(q0.cpu().numpy()[:2] - rq).max() <= tau
-    np.testing.assert_allclose(prob.cpu().numpy()[:2], rp, rtol=1e-3)
+    np.testing.assert_allclose(logp.cpu().numpy()[:2], np.log(rp), rtol=0, atol=1e-3)
     assert np.all(np.where(b == 0, u[:2] < rq + tau, u[:2] >= rq - tau))
+
+
+def test_fp32_k3_1152_modes():
+    """K = 3 at the 1152-mode size of a 144-mode interferometer read out through 8
+    time bins (a lossy 1152-mode instance of the same model): finite
+    probabilities, and one sample scored by the oracle."""
+    M = 1152
+    inst = synthetic.random_instance(M, 3, seed=1152, r_range=(0.3, 0.9), eta_range=(0.2, 0.4), n_squeezed=576)
+    kap = kappa_of(inst, 3)
+    u = uniforms(128, M, seed=1152)
+    bits, logp, q0 = gbs.sample(kap, M, 3, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+                                want_q0=True)
+    assert bool(torch.isfinite(logp).all())
+    b = bits.cpu().numpy()[:1]
+    _, rp, rq = oracle.sample(kap.cpu().numpy(), M, 3, force=b)
+    tau = 2e-4
+    assert np.abs(q0.cpu().numpy()[:1] - rq).max() <= tau
+    np.testing.assert_allclose(logp.cpu().numpy()[:1], np.log(rp), rtol=0, atol=5e-3)
+    assert np.all(np.where(b == 0, u[:1] < rq + tau, u[:1] >= rq - tau))
 
 
 def test_invalid_arguments():
@@ -108,4 +127,5 @@ def test_invalid_arguments():
         gbs.sample(kap, 8, 5, u=u, orders=(4, 3, 2))
     assert gbs.sampler_workspace_bytes(8, 6, 128) == 0
     assert gbs.sampler_workspace_bytes(4, 5, 128) == 0
+    assert gbs.sampler_workspace_bytes(1025, 5, 128) == 0 and gbs.sampler_workspace_bytes(1152, 3, 128) > 0
     assert gbs.sampler_workspace_bytes(8, 5, 64) == 0
