@@ -84,6 +84,7 @@ struct Args {
     R *CA, *CB, *CC;       // per-step coefficients [i][S]: chi_i Pp~[n-1][i+1], kappa(i,n) chi_i, kappa(i,n) chi_i Pp~[n-1][i+1]
     R *T;                  // [C(M,2)][2][S] per-pair parts of the p1 order-3 term (see p2_kernel)
     const R *hs;           // per-variable half scale s_v / 2, hs[v], v = 1..M
+    const R *lead;         // per-variable pairs (kappa'({v}), hs[v]) at lead[2v], lead[2v+1]
     const double *H;       // per-variable log scale ln s_v (the click entropy of mode v - 1)
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
@@ -125,6 +126,23 @@ struct Spins {
         return (cur >> (v & 31)) & 1u ? R(-1) : R(1);
     }
 };
+
+// (kappa'({n}), hs_n) in one vector load: the leading coefficient of every rule
+// at step n is hs_n + chi_n kappa'({n}).
+template <class R>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    using T = float2;
+};
+template <>
+struct Pair2<double> {
+    using T = double2;
+};
+template <class R>
+__device__ __forceinline__ typename Pair2<R>::T lead(const Args<R> &a, int n) {
+    return reinterpret_cast<const typename Pair2<R>::T *>(a.lead)[n];
+}
 
 // kappa of the sorted variable set (v_1 < .. < v_d), 1-based.
 template <class R>
@@ -363,7 +381,8 @@ __global__ void bias_kernel(Args<R> a, int n) {
         for (int i = 3; i < n; ++i)
             B = fma(sp(i) * pp(a, n - 1, i + 1, s), K == 5 ? Yv[(size_t)i * a.S + s] : a.Z[i_z(i, n) * a.S + s], B);
     }
-    const R p0 = fma(a.hs[n], Pm, B), p1v = fma(a.hs[n], Pm, -B);
+    const R hn = lead(a, n).y;
+    const R p0 = fma(hn, Pm, B), p1v = fma(hn, Pm, -B);
     const R c0 = p0 > R(0) ? p0 : R(0), c1 = p1v > R(0) ? p1v : R(0);
     const R q = (c0 + c1 > R(0)) ? c0 / (c0 + c1) : R(0.5);
     int x = 0;
@@ -414,7 +433,8 @@ __global__ void __launch_bounds__(ETB) pp_kernel(Args<R> a, int n) {
                 acc = fma(k2(a, i, n) * sp(i) * pp(a, n - 1, i + 1, s), pp(a, i - 1, l, s), acc);
         if (a.opp >= 3)
             for (int j = l; j < n - 1; ++j) acc = fma(a.Y[(size_t)j * a.S + s], pp(a, j - 1, l, s), acc);
-        a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * pp(a, n - 1, l, s));
+        const auto ld = lead(a, n);
+        a.Pp[i_pp(n, l) * a.S + s] = fma(cn, acc, fma(ld.x, cn, ld.y) * pp(a, n - 1, l, s));
     }
 }
 
@@ -461,7 +481,8 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
             for (int d = 1; d < e; ++d) acc = fma(sd(d), T[(2 * (cb(e - 1, 2) + (uint64_t)(d - 1))) * S], acc);
             for (int j = e + 1; j < n; ++j) acc = fma(sd(j), T[(2 * (cb(j - 1, 2) + (uint64_t)(e - 1)) + 1) * S], acc);
         }
-        a.P1[i_p1(n, e) * S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * p1(a, n - 1, e, s));
+        const auto ld = lead(a, n);
+        a.P1[i_p1(n, e) * S + s] = fma(cn, acc, fma(ld.x, cn, ld.y) * p1(a, n - 1, e, s));
     }
 }
 
@@ -544,7 +565,8 @@ __global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
             a.T[o * S + s] = tE;
             a.T[(o + 1) * S + s] = tD;
         }
-        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, fma(k1(a, n), cn, a.hs[n]) * p2(a, n - 1, e, d, s));
+        const auto ld = lead(a, n);
+        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, fma(ld.x, cn, ld.y) * p2(a, n - 1, e, d, s));
     }
 }
 
@@ -573,15 +595,18 @@ __global__ void logp_kernel(Args<R> a, double *logp) {
 // so mode v - 1 is silent with probability (1 + c_v) / 2; s_v = exp(H_v) with H_v
 // that binary entropy in nats (s_v in [1, 2]).
 template <class R>
-__global__ void scale_kernel(const double *__restrict__ kap, int M, R *hs, double *H) {
+__global__ void scale_kernel(const double *__restrict__ kap, int M, R *hs, R *lead, double *H) {
     const int v = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     if (v > M) return;
     double p0 = 0.5 * (1.0 + kap[v - 1]);
     p0 = p0 < 0.0 ? 0.0 : (p0 > 1.0 ? 1.0 : p0);
     const double p1 = 1.0 - p0;
     const double h = (p0 > 0.0 ? -p0 * log(p0) : 0.0) + (p1 > 0.0 ? -p1 * log(p1) : 0.0);
+    const double half = 0.5 * exp(h);
     H[v] = h;
-    hs[v] = (R)(0.5 * exp(h));
+    hs[v] = (R)half;
+    lead[2 * v] = (R)(kap[v - 1] * half);
+    lead[2 * v + 1] = (R)half;
 }
 
 // kappa'(S) = kappa(S) prod_{v in S} s_v / 2 for every table entry, in the
@@ -646,6 +671,8 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     off = a256(off + ((size_t)M + 1) * es);
     L.H = off;
     off = a256(off + ((size_t)M + 1) * sizeof(double));
+    L.lead = off;
+    off = a256(off + 2 * ((size_t)M + 1) * es);
     L.total = off;
     return L;
 }
@@ -724,8 +751,9 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     {
         R *hs = reinterpret_cast<R *>(w + L.hs);
         double *H = reinterpret_cast<double *>(w + L.H);
+        R *ldp = reinterpret_cast<R *>(w + L.lead);
         R *kf = reinterpret_cast<R *>(w + L.kap);
-        scale_kernel<R><<<(c.M + 255) / 256, 256, 0, st>>>(c.kappa, c.M, hs, H);
+        scale_kernel<R><<<(c.M + 255) / 256, 256, 0, st>>>(c.kappa, c.M, hs, ldp, H);
         uint64_t off = 0;
         for (int d = 1; d <= c.K; ++d) {
             const uint64_t n = cb(c.M, d), threads = (n + KS_CHUNK - 1) / KS_CHUNK;
@@ -734,6 +762,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
         }
         a.kap = kf;
         a.hs = hs;
+        a.lead = ldp;
         a.H = H;
     }
     for (int s0 = 0; s0 < c.n_samples; s0 += c.S) {
