@@ -389,20 +389,27 @@ def bench_sampler(args):
     """Stage 2: K = 5 double-elision samples of the M=144 workload's spin-cumulant
     table (FP32 tables, as the paper stores them), one gbs_sample call of --batch
     samples per step; uniforms seeded and resident on the device. The FP64 form is
-    timed beside it on a smaller batch."""
+    timed beside it on a smaller batch. Under torchrun every rank draws its own
+    samples (rank-seeded uniforms, no exchange): weak scaling, the slowest rank's
+    time, all ranks' samples."""
     import torch
     import synthetic
     import paper_2511_14923_gb300 as gbs
+    rank, world, dist = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     gbs.build()
     M, K, B = 144, 5, args.batch
     inst = synthetic.config(2)
     kap = gbs.spin_cumulants(torch.from_numpy(inst.V).cuda(), K, "fp64")
-    g = torch.Generator(device="cuda").manual_seed(20251114)
+    g = torch.Generator(device="cuda").manual_seed(20251114 + 1000 * rank)
     steps, warm = args.steps, max(args.warmup, 3)
     us = [torch.rand(B, M, dtype=torch.float64, device="cuda", generator=g) for _ in range(steps + warm)]
     ws = torch.empty(gbs.sampler_workspace_bytes(M, K, B, "fp32"), dtype=torch.uint8, device="cuda")
     for w in range(warm):
         gbs.sample(kap, M, K, u=us[w], batch=B, precision="fp32", workspace=ws, check=False)
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler() as clk:
@@ -412,7 +419,9 @@ def bench_sampler(args):
                                        check=False)
             b.record()
         torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dist, torch.device("cuda", local))
     ok = bool(torch.isfinite(logp).all())
     # end to end: uniforms from pinned host memory in, bitstrings out, every step
     uh = us[0].cpu().pin_memory()
@@ -426,7 +435,7 @@ def bench_sampler(args):
         bh.copy_(bits, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / steps
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps, dist, torch.device("cuda", local))
     # FP64 tables on a smaller batch
     B64 = 512
     ws64 = torch.empty(gbs.sampler_workspace_bytes(M, K, B64, "fp64"), dtype=torch.uint8, device="cuda")
@@ -436,19 +445,23 @@ def bench_sampler(args):
     e1.record()
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1)
-    value = B / (ms * 1e-3)
+    value = B * world / (ms * 1e-3)
+    if rank != 0:
+        return
     print(json.dumps({
         "metric": "samples/s, K=5 double-elision chain-rule sampler, M=144", "value": value, "unit": "samples/s",
-        "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+        "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "spin cumulants of the M=144 kmax=5 workload (72 squeezers, per-mode eta), "
-                               "K=5 double elision, orders (3, 3, 2), FP32 tables", "samples_per_step": B,
+                               "K=5 double elision, orders (3, 3, 2), FP32 tables", "samples_per_step_per_gpu": B,
+                   "parallelism": f"{world} independent sampler(s), rank-seeded uniforms, no exchange",
                    "inputs": f"{B} x {M} seeded uniforms per step, resident on the device",
                    "workspace_GB": ws.numel() / 1e9, "l2": "per-step working set (tables of 8192 samples) >> L2"},
         "paper_context": {"samples_per_s_per_gpu": PAPER_SAMPLES_PER_GPU_S,
-                          "hardware": "8x H100 SXM, 1e7 samples in 115 min", "ratio": value / PAPER_SAMPLES_PER_GPU_S},
+                          "hardware": "8x H100 SXM, 1e7 samples in 115 min",
+                          "ratio_per_gpu": value / world / PAPER_SAMPLES_PER_GPU_S},
         "fp64_tables": {"samples_per_step": B64, "ms_per_step": ms64, "value": B64 / (ms64 * 1e-3)},
-        "e2e": {"value": B / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": B * M * 8,
+        "e2e": {"value": B * world / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": B * M * 8,
                 "d2h_bytes_per_step": B * M},
         "all_finite": ok, "clocks": clk.summary()}), flush=True)
 
