@@ -53,6 +53,7 @@
 // always touches 32 consecutive samples of one entry.
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 
 #include "gbs.h"
 #include "gbs_common.cuh"
@@ -86,6 +87,8 @@ struct Args {
     const R *hs;           // per-variable half scale s_v / 2, hs[v], v = 1..M
     const R *lead;         // per-variable pairs (kappa'({v}), hs[v]) at lead[2v], lead[2v+1]
     const double *H;       // per-variable log scale ln s_v (the click entropy of mode v - 1)
+    unsigned *status;      // status word (ST_* bits), first bytes of the workspace
+    int use_tc;            // FP32: step product on the tensor cores
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -347,6 +350,194 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t r
 #pragma unroll
         for (int j = 0; j < TN; ++j) out[s0 + (j < 4 ? 0 : BNt / 2) + tx * 4 + (j & 3)] = acc[i][j];
     }
+}
+
+// ---------------------------------------------------------------- step product on the tensor cores
+// FP32 calls run the step product on the 5th-generation tensor cores: tcgen05.mma
+// kind::tf32 with the 3-term split x = hi + lo (hi, lo TF32), Z = Ahi Bhi + Ahi Blo
+// + Alo Bhi accumulated in FP32 in tensor memory (the dropped Alo Blo term is
+// ~2^-22 relative). A CTA of 128 threads owns 128 rows x 128 samples; thread i
+// stages row i of the cumulant segments and sample i of W into shared memory
+// (K-major core matrices of 8 rows x 16 bytes, no swizzle), one elected thread
+// issues the MMAs, and a two-stage ring with one mbarrier per stage overlaps the
+// staging of chunk c+1 with the MMAs of chunk c. Every wait is bounded; a wait
+// that runs out sets ST_TIMEOUT in the status word and the CTA stops.
+constexpr int TC_M = 128, TC_N = 128, TC_KC = 32;
+constexpr int TC_OPB = TC_M * TC_KC * 4;  // bytes of one operand copy per stage
+constexpr int TC_STAGE = 4 * TC_OPB;      // A hi, A lo, B hi, B lo
+constexpr int TC_SMEM = 2 * TC_STAGE + 256;
+// instruction descriptor: D f32, A and B tf32, both K-major, N = 128, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row r, inner k) of a 128 x 32 operand copy
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {
+    const int core = (r >> 3) * (TC_KC / 4) + (k >> 2);  // core matrix: 8-row group, then 4-wide K slice
+    return (uint32_t)((core * 8 + (r & 7)) * 16 + (k & 3) * 4);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle; leading byte offset 128
+// (next core matrix along K), stride byte offset 1024 (next group of 8 rows)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint64_t rows, int D) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 64);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint64_t m0 = (uint64_t)blockIdx.x * TC_M;
+    const int s0 = blockIdx.y * TC_N;
+    uint64_t kb = 0, dst = 0;
+    int kind = -1;
+    if (m0 + tid < rows) zrow(K, a.M, t, m0 + tid, a.off, kb, kind, dst);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t sbase = smem_u32(smem);
+    const int nk = (D + TC_KC - 1) / TC_KC;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+    const float *kp = a.kap + kb;
+    const float *wp = a.W + s0 + tid;
+    for (int c = 0; c < nk && ok; ++c) {
+        const int st = c & 1;
+        if (c >= 2) {  // the MMAs of chunk c-2 read this stage
+            ok = mbar_wait(&mbar[st], phase[st]);
+            phase[st] ^= 1u;
+            if (!ok) break;
+        }
+        unsigned char *sp = smem + st * TC_STAGE;
+        const int k0 = c * TC_KC;
+#pragma unroll 8
+        for (int k = 0; k < TC_KC; ++k) {
+            const float v = (kind >= 0 && k0 + k < D) ? kp[k0 + k] : 0.f;
+            const float hi = to_tf32(v);
+            const uint32_t o = tc_off(tid, k);
+            *reinterpret_cast<float *>(sp + o) = hi;
+            *reinterpret_cast<float *>(sp + TC_OPB + o) = to_tf32(v - hi);
+            const float w = (k0 + k < D) ? wp[(size_t)(k0 + k) * a.S] : 0.f;
+            const float whi = to_tf32(w);
+            *reinterpret_cast<float *>(sp + 2 * TC_OPB + o) = whi;
+            *reinterpret_cast<float *>(sp + 3 * TC_OPB + o) = to_tf32(w - whi);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t sb = sbase + st * TC_STAGE;
+#pragma unroll
+            for (int j = 0; j < TC_KC / 8; ++j) {
+                const uint32_t o = j * 256;  // two core matrices per 8-wide slice of K
+                const uint64_t ahi = tc_desc(sb + o), alo = tc_desc(sb + TC_OPB + o);
+                const uint64_t bhi = tc_desc(sb + 2 * TC_OPB + o), blo = tc_desc(sb + 3 * TC_OPB + o);
+                tc_mma(tmem, ahi, bhi, (c > 0 || j > 0) ? 1u : 0u);
+                tc_mma(tmem, ahi, blo, 1u);
+                tc_mma(tmem, alo, bhi, 1u);
+            }
+            tc_commit(&mbar[st]);
+        }
+    }
+    // wait for the chunks whose completion has not been waited for
+    for (int c = (nk >= 2 ? nk - 2 : 0); c < nk && ok; ++c) {
+        const int st = c & 1;
+        ok = mbar_wait(&mbar[st], phase[st]);
+        phase[st] ^= 1u;
+    }
+    if (!ok) {
+        if (a.status) atomicOr(a.status, ST_TIMEOUT);
+    } else {
+        tc_fence_after();
+        float *out = kind == 0 ? a.G
+                   : kind == 1 ? a.Z + dst * a.S
+                   : kind == 2 ? a.Z5 + dst * a.S
+                               : a.X + dst * a.S;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int cc = 0; cc < TC_N / 32; ++cc) {
+            uint32_t v[32];
+            tc_ld32(lane_base + (uint32_t)(cc * 32), v);
+            if (kind >= 0) {
+                float4 *o4 = reinterpret_cast<float4 *>(out + s0 + cc * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    o4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                        __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
 }
 
 // ---------------------------------------------------------------- step n: bias and draw
@@ -643,7 +834,7 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     SamplerLayout L{};
     const size_t es = precision == 0 ? sizeof(double) : sizeof(float);
     const size_t Ss = (size_t)S;
-    size_t off = 0;
+    size_t off = 256;  // status word first (read by gbs_stream_status)
     auto take = [&](size_t &field, size_t entries) {
         field = off;
         off = a256(off + entries * Ss * es);
@@ -702,8 +893,18 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
             const uint64_t rows = K == 3   ? 1 + (uint64_t)(M - t)
                                   : K == 4 ? 1 + 2 * (uint64_t)(M - t)
                                            : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
-            dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
-            zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
+            if constexpr (sizeof(R) == 4) {
+                if (a.use_tc) {
+                    dim3 grid((unsigned)((rows + TC_M - 1) / TC_M), (unsigned)(S / TC_N));
+                    ztc_kernel<K><<<grid, 128, TC_SMEM, st>>>(a, t, rows, D);
+                } else {
+                    dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
+                    zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
+                }
+            } else {
+                dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
+                zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
+            }
         }
         if (K == 5 && t > 3) y_kernel<R><<<egrid(S, (uint64_t)(t - 3)), ETB, 0, st>>>(a, t);
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
@@ -748,6 +949,23 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.CC = a.CB + ((size_t)c.M + 1) * c.S;
     a.T = reinterpret_cast<R *>(w + L.T);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
+    a.status = reinterpret_cast<unsigned *>(w);
+    {
+        cudaError_t e = cudaMemsetAsync(w, 0, 256, st);
+        if (e != cudaSuccess) return e;
+    }
+    a.use_tc = 0;
+    if (sizeof(R) == 4) {
+        const char *env = getenv("GBS_SAMPLER_SIMT");
+        a.use_tc = (env && *env && *env != '0') ? 0 : 1;
+        if (a.use_tc) {
+            cudaError_t e = cudaSuccess;
+            if (c.K == 3) e = cudaFuncSetAttribute(ztc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            if (c.K == 4) e = cudaFuncSetAttribute(ztc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            if (c.K == 5) e = cudaFuncSetAttribute(ztc_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            if (e != cudaSuccess) return e;
+        }
+    }
     {
         R *hs = reinterpret_cast<R *>(w + L.hs);
         double *H = reinterpret_cast<double *>(w + L.H);

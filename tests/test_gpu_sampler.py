@@ -129,3 +129,21 @@ def test_invalid_arguments():
     assert gbs.sampler_workspace_bytes(4, 5, 128) == 0
     assert gbs.sampler_workspace_bytes(1025, 5, 128) == 0 and gbs.sampler_workspace_bytes(1152, 3, 128) > 0
     assert gbs.sampler_workspace_bytes(8, 5, 64) == 0
+
+
+def test_fp32_tensor_core_product_matches_simt(monkeypatch):
+    """FP32 calls run the step product on the tensor cores (tcgen05, 3-term TF32
+    split); GBS_SAMPLER_SIMT=1 selects the CUDA-core product. Same uniforms: the
+    log-probabilities agree to FP32 rounding and the decisions agree except within
+    the q0 tolerance of the FP32 tests."""
+    M, K = 40, 5
+    inst = synthetic.random_instance(M, K, seed=4040, r_range=(0.6, 1.4), eta_range=(0.3, 0.5))
+    kap = kappa_of(inst, K)
+    u = torch.from_numpy(uniforms(256, M, seed=5)).cuda()
+    b_tc, l_tc, q_tc = gbs.sample(kap, M, K, u=u, batch=256, precision="fp32", want_q0=True)
+    monkeypatch.setenv("GBS_SAMPLER_SIMT", "1")
+    b_s, l_s, q_s = gbs.sample(kap, M, K, u=u, batch=256, precision="fp32", want_q0=True)
+    same = (b_tc == b_s).all(dim=1)
+    assert float(same.float().mean()) > 0.9
+    assert torch.abs(l_tc[same] - l_s[same]).max().item() <= 1e-3
+    assert torch.abs(q_tc[same] - q_s[same]).max().item() <= 2e-4
