@@ -353,26 +353,30 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t r
 }
 
 // ---------------------------------------------------------------- step product on the tensor cores
-// FP32 calls run the step product on the 5th-generation tensor cores: tcgen05.mma
-// kind::tf32 with the 3-term split x = hi + lo (hi, lo TF32), Z = Ahi Bhi + Ahi Blo
-// + Alo Bhi accumulated in FP32 in tensor memory (the dropped Alo Blo term is
-// ~2^-22 relative). A CTA of 128 threads owns 128 rows x 128 samples; thread i
-// stages row i of the cumulant segments and sample i of W into shared memory
-// (K-major core matrices of 8 rows x 16 bytes, no swizzle), one elected thread
-// issues the MMAs, and a two-stage ring with one mbarrier per stage overlaps the
-// staging of chunk c+1 with the MMAs of chunk c. Every wait is bounded; a wait
-// that runs out sets ST_TIMEOUT in the status word and the CTA stops.
-constexpr int TC_M = 128, TC_N = 128, TC_KC = 32;
-constexpr int TC_OPB = TC_M * TC_KC * 4;  // bytes of one operand copy per stage
-constexpr int TC_STAGE = 4 * TC_OPB;      // A hi, A lo, B hi, B lo
+// FP32 calls with a batch that is a multiple of 256 run the step product on the
+// 5th-generation tensor cores: tcgen05.mma kind::tf32 with the 3-term split
+// x = hi + lo (hi, lo TF32), Z = Ahi Bhi + Ahi Blo + Alo Bhi accumulated in FP32
+// in tensor memory (the dropped Alo Blo term is ~2^-22 relative). A CTA of 128
+// threads owns 128 rows x 256 samples. W arrives from wtc_kernel already split
+// and laid out as the MMA's K-major core matrices (8 rows x 16 bytes, no
+// swizzle), one contiguous 64 KB block per 32-wide K chunk and sample tile, and
+// is brought in by one TMA bulk copy per chunk; thread i splits and stages row i
+// of the cumulant segments. One elected thread issues the MMAs. Two stages, each
+// with a "full" mbarrier (the bulk copy's bytes) and an "empty" one (the MMAs'
+// commit), overlap the staging of chunk c+1 with the MMAs of chunk c. Every wait
+// is bounded; one that runs out sets ST_TIMEOUT in the status word.
+constexpr int TC_M = 128, TC_N = 256, TC_KC = 32;
+constexpr int TC_AB = TC_M * TC_KC * 4;         // bytes of one A copy per stage (16 KB)
+constexpr int TC_BB = TC_N * TC_KC * 4;         // bytes of one B copy per stage (32 KB)
+constexpr int TC_STAGE = 2 * TC_AB + 2 * TC_BB;  // A hi, A lo, B hi, B lo
 constexpr int TC_SMEM = 2 * TC_STAGE + 256;
-// instruction descriptor: D f32, A and B tf32, both K-major, N = 128, M = 128
+// instruction descriptor: D f32, A and B tf32, both K-major, N = 256, M = 128
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (row r, inner k) of a 128 x 32 operand copy
+// byte offset of element (row r, inner k) of an operand copy with 32-wide K
 __device__ __forceinline__ uint32_t tc_off(int r, int k) {
     const int core = (r >> 3) * (TC_KC / 4) + (k >> 2);  // core matrix: 8-row group, then 4-wide K slice
     return (uint32_t)((core * 8 + (r & 7)) * 16 + (k & 3) * 4);
@@ -409,6 +413,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
     return false;
 }
 
+// one TMA bulk copy global -> shared, completing `bytes` on the mbarrier
+__device__ __forceinline__ void tma_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -437,20 +450,73 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// W_t split into TF32 hi / lo in the tensor-core tile layout: element (r, s),
+// r < 32 ceil(D / 32) (zero beyond D), at float offset
+// ((c nsb + sb) 2 + part) 8192 + tc_off(s % 256, r % 32) / 4, c = r / 32,
+// sb = s / 256, nsb = S / 256. A thread forms four consecutive r (one 16-byte
+// row of a core matrix) of one sample, so 8 consecutive samples write one
+// 128-byte line. Grid: (samples / ETB, quads of r).
+template <int K>
+__global__ void __launch_bounds__(ETB) wtc_kernel(Args<float> a, int t, int D) {
+    const int s = blockIdx.x * ETB + threadIdx.x;
+    const int Dp = (D + TC_KC - 1) / TC_KC * TC_KC;
+    const int nsb = a.S / TC_N, sb = s / TC_N, sl = s % TC_N;
+    Spins<float> sp(a, s), sd(a, s);
+    for (int qd = blockIdx.y; qd < Dp / 4; qd += gridDim.y) {
+        const int r0 = 4 * qd;
+        float v[4];
+        int e = 0, d = 0;
+        if (K != 3 && r0 < D) {
+            int hi, lo;
+            pair_of((uint64_t)r0, hi, lo);
+            e = hi + 1;
+            d = lo + 1;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + j;
+            v[j] = 0.f;
+            if (r < D) {
+                if (K == 3) {
+                    v[j] = p1(a, t - 1, r + 1, s) * sp(r + 1);
+                } else {
+                    v[j] = p2(a, t - 1, e, d, s) * sp(e) * sd(d);
+                    if (++d == e) {  // next pair in colex order
+                        ++e;
+                        d = 1;
+                    }
+                }
+            }
+        }
+        float4 h, l;
+        h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
+        h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
+        h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
+        h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
+        const size_t blk = ((size_t)(r0 / TC_KC) * nsb + sb) * 2 * 8192;
+        const uint32_t o = tc_off(sl, r0 % TC_KC) / 4;
+        *reinterpret_cast<float4 *>(a.W + blk + o) = h;
+        *reinterpret_cast<float4 *>(a.W + blk + 8192 + o) = l;
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint64_t rows, int D) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
+    uint64_t *empty = full + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 64);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint64_t m0 = (uint64_t)blockIdx.x * TC_M;
-    const int s0 = blockIdx.y * TC_N;
+    const int sb = blockIdx.y, s0 = sb * TC_N, nsb = a.S / TC_N;
     uint64_t kb = 0, dst = 0;
     int kind = -1;
     if (m0 + tid < rows) zrow(K, a.M, t, m0 + tid, a.off, kb, kind, dst);
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -465,56 +531,63 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
     const uint32_t tmem = *tslot;
     const uint32_t sbase = smem_u32(smem);
     const int nk = (D + TC_KC - 1) / TC_KC;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t ph_full[2] = {0u, 0u}, ph_empty[2] = {0u, 0u};
     bool ok = true;
     const float *kp = a.kap + kb;
-    const float *wp = a.W + s0 + tid;
     for (int c = 0; c < nk && ok; ++c) {
         const int st = c & 1;
         if (c >= 2) {  // the MMAs of chunk c-2 read this stage
-            ok = mbar_wait(&mbar[st], phase[st]);
-            phase[st] ^= 1u;
+            ok = mbar_wait(&empty[st], ph_empty[st]);
+            ph_empty[st] ^= 1u;
             if (!ok) break;
         }
         unsigned char *sp = smem + st * TC_STAGE;
+        if (tid == 0) tma_bulk(sp + 2 * TC_AB, a.W + ((size_t)c * nsb + sb) * 2 * 8192, 2 * TC_BB, &full[st]);
         const int k0 = c * TC_KC;
-#pragma unroll 8
-        for (int k = 0; k < TC_KC; ++k) {
-            const float v = (kind >= 0 && k0 + k < D) ? kp[k0 + k] : 0.f;
-            const float hi = to_tf32(v);
+#pragma unroll 2
+        for (int k = 0; k < TC_KC; k += 4) {
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = (kind >= 0 && k0 + k + j < D) ? kp[k0 + k + j] : 0.f;
+            float4 h, l;
+            h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
+            h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
+            h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
+            h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
             const uint32_t o = tc_off(tid, k);
-            *reinterpret_cast<float *>(sp + o) = hi;
-            *reinterpret_cast<float *>(sp + TC_OPB + o) = to_tf32(v - hi);
-            const float w = (k0 + k < D) ? wp[(size_t)(k0 + k) * a.S] : 0.f;
-            const float whi = to_tf32(w);
-            *reinterpret_cast<float *>(sp + 2 * TC_OPB + o) = whi;
-            *reinterpret_cast<float *>(sp + 3 * TC_OPB + o) = to_tf32(w - whi);
+            *reinterpret_cast<float4 *>(sp + o) = h;
+            *reinterpret_cast<float4 *>(sp + TC_AB + o) = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            tc_fence_after();
-            const uint32_t sb = sbase + st * TC_STAGE;
+            ok = mbar_wait(&full[st], ph_full[st]);
+            ph_full[st] ^= 1u;
+            if (ok) {
+                tc_fence_after();
+                const uint32_t sbs = sbase + st * TC_STAGE;
 #pragma unroll
-            for (int j = 0; j < TC_KC / 8; ++j) {
-                const uint32_t o = j * 256;  // two core matrices per 8-wide slice of K
-                const uint64_t ahi = tc_desc(sb + o), alo = tc_desc(sb + TC_OPB + o);
-                const uint64_t bhi = tc_desc(sb + 2 * TC_OPB + o), blo = tc_desc(sb + 3 * TC_OPB + o);
-                tc_mma(tmem, ahi, bhi, (c > 0 || j > 0) ? 1u : 0u);
-                tc_mma(tmem, ahi, blo, 1u);
-                tc_mma(tmem, alo, bhi, 1u);
+                for (int j = 0; j < TC_KC / 8; ++j) {
+                    const uint32_t o = j * 256;  // two core matrices per 8-wide slice of K
+                    const uint64_t ahi = tc_desc(sbs + o), alo = tc_desc(sbs + TC_AB + o);
+                    const uint64_t bhi = tc_desc(sbs + 2 * TC_AB + o), blo = tc_desc(sbs + 2 * TC_AB + TC_BB + o);
+                    tc_mma(tmem, ahi, bhi, (c > 0 || j > 0) ? 1u : 0u);
+                    tc_mma(tmem, ahi, blo, 1u);
+                    tc_mma(tmem, alo, bhi, 1u);
+                }
+                tc_commit(&empty[st]);
             }
-            tc_commit(&mbar[st]);
         }
+        ok = __syncthreads_and(ok);
     }
-    // wait for the chunks whose completion has not been waited for
+    // wait for the chunks whose MMAs have not been waited for
     for (int c = (nk >= 2 ? nk - 2 : 0); c < nk && ok; ++c) {
         const int st = c & 1;
-        ok = mbar_wait(&mbar[st], phase[st]);
-        phase[st] ^= 1u;
+        ok = mbar_wait(&empty[st], ph_empty[st]);
+        ph_empty[st] ^= 1u;
     }
     if (!ok) {
-        if (a.status) atomicOr(a.status, ST_TIMEOUT);
+        if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
     } else {
         tc_fence_after();
         float *out = kind == 0 ? a.G
@@ -522,7 +595,7 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
                    : kind == 2 ? a.Z5 + dst * a.S
                                : a.X + dst * a.S;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
+#pragma unroll 1
         for (int cc = 0; cc < TC_N / 32; ++cc) {
             uint32_t v[32];
             tc_ld32(lane_base + (uint32_t)(cc * 32), v);
@@ -849,7 +922,8 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.G, 1);
     take(L.Y, K >= 4 ? (size_t)M + 1 : 0);
     take(L.X, K >= 4 ? cb(M, 2) : 0);
-    take(L.W, K >= 4 ? cb(M - 1, 2) : (size_t)M);
+    // W: plain [r][S], or for the tensor-core product hi / lo copies of 32-padded chunks
+    take(L.W, 2 * ((K >= 4 ? cb(M - 1, 2) : (size_t)M) + 32));
     take(L.CA, K >= 4 ? 3 * ((size_t)M + 1) : 0);
     take(L.T, K >= 4 ? 2 * cb(M - 1, 2) : 0);
     L.bw = off;
@@ -889,12 +963,17 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         // products for this step and later ones (inputs: rows < t of the tables)
         const int D = K == 3 ? t - 1 : (int)cb(t - 1, 2);  // K = 4, 5: pairs below t
         if (D > 0) {
-            w_kernel<R, K><<<egrid(S, (uint64_t)D), ETB, 0, st>>>(a, t, D);
+            bool tc = false;
+            if constexpr (sizeof(R) == 4) tc = a.use_tc != 0;
+            if constexpr (sizeof(R) == 4) {
+                if (tc) wtc_kernel<K><<<egrid(S, (uint64_t)((D + TC_KC - 1) / TC_KC * TC_KC / 4)), ETB, 0, st>>>(a, t, D);
+            }
+            if (!tc) w_kernel<R, K><<<egrid(S, (uint64_t)D), ETB, 0, st>>>(a, t, D);
             const uint64_t rows = K == 3   ? 1 + (uint64_t)(M - t)
                                   : K == 4 ? 1 + 2 * (uint64_t)(M - t)
                                            : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
             if constexpr (sizeof(R) == 4) {
-                if (a.use_tc) {
+                if (tc) {
                     dim3 grid((unsigned)((rows + TC_M - 1) / TC_M), (unsigned)(S / TC_N));
                     ztc_kernel<K><<<grid, 128, TC_SMEM, st>>>(a, t, rows, D);
                 } else {
@@ -957,7 +1036,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.use_tc = 0;
     if (sizeof(R) == 4) {
         const char *env = getenv("GBS_SAMPLER_SIMT");
-        a.use_tc = (env && *env && *env != '0') ? 0 : 1;
+        a.use_tc = (env && *env && *env != '0') || c.S % TC_N != 0 ? 0 : 1;
         if (a.use_tc) {
             cudaError_t e = cudaSuccess;
             if (c.K == 3) e = cudaFuncSetAttribute(ztc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);

@@ -70,7 +70,7 @@ def test_fp32_decisions_consistent_with_oracle(K, M):
     kap = kappa_of(inst, K)
     n = 256
     u = uniforms(n, M, seed=11)
-    bits, logp, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+    bits, logp, q0 = gbs.sample(kap, M, K, u=torch.from_numpy(u).cuda(), batch=256, precision="fp32",
                                 want_q0=True)
     b = bits.cpu().numpy()
     _, rp, rq = oracle.sample(kap.cpu().numpy(), M, K, force=b)
@@ -87,7 +87,7 @@ def test_fp32_m144_k5_consistent_on_a_few_samples():
     kap = kappa_of(inst, 5)
     n = 64
     u = uniforms(n, 144, seed=144)
-    bits, logp, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+    bits, logp, q0 = gbs.sample(kap, 144, 5, u=torch.from_numpy(u).cuda(), batch=256, precision="fp32",
                                 want_q0=True)
     assert bool(torch.isfinite(logp).all())
     b = bits.cpu().numpy()[:2]
@@ -106,7 +106,7 @@ def test_fp32_k3_1152_modes():
     inst = synthetic.random_instance(M, 3, seed=1152, r_range=(0.3, 0.9), eta_range=(0.2, 0.4), n_squeezed=576)
     kap = kappa_of(inst, 3)
     u = uniforms(128, M, seed=1152)
-    bits, logp, q0 = gbs.sample(kap, M, 3, u=torch.from_numpy(u).cuda(), batch=128, precision="fp32",
+    bits, logp, q0 = gbs.sample(kap, M, 3, u=torch.from_numpy(u).cuda(), batch=256, precision="fp32",
                                 want_q0=True)
     assert bool(torch.isfinite(logp).all())
     b = bits.cpu().numpy()[:1]
