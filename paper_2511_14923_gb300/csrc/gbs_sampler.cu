@@ -84,6 +84,7 @@ struct Args {
     R *chi, *P, *Pp, *P1, *P2, *Z, *Z5, *G, *Y, *X, *W;
     R *CA, *CB, *CC;       // per-step coefficients [i][S]: chi_i Pp~[n-1][i+1], kappa(i,n) chi_i, kappa(i,n) chi_i Pp~[n-1][i+1]
     R *T;                  // [C(M,2)][2][S] per-pair parts of the p1 order-3 term (see p2_kernel)
+    float *At;             // tensor-core product: the step's rows, split and tiled (atc_kernel)
     const R *hs;           // per-variable half scale s_v / 2, hs[v], v = 1..M
     const R *lead;         // per-variable pairs (kappa'({v}), hs[v]) at lead[2v], lead[2v+1]
     const double *H;       // per-variable log scale ln s_v (the click entropy of mode v - 1)
@@ -413,9 +414,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
     return false;
 }
 
-// one TMA bulk copy global -> shared, completing `bytes` on the mbarrier
-__device__ __forceinline__ void tma_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+// TMA bulk copies global -> shared that complete their bytes on an mbarrier;
+// the expected byte count is announced once per phase.
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
@@ -500,23 +504,59 @@ __global__ void __launch_bounds__(ETB) wtc_kernel(Args<float> a, int t, int D) {
     }
 }
 
+// The rows of the step product (cumulant segments) split into TF32 hi / lo and
+// laid out like W: row tile rt (128 rows), chunk c (32 inner entries) at float
+// offset (rt nk + c) 2 4096, hi then lo, each in the core-matrix layout.
+// Rows beyond `rows` and entries beyond D are zero. Grid: (row tiles, chunks),
+// 128 threads, thread i = row i of the tile.
+template <int K>
+__global__ void __launch_bounds__(128) atc_kernel(Args<float> a, int t, uint64_t rows, int D) {
+    const int tid = threadIdx.x, rt = blockIdx.x, c = blockIdx.y, nk = gridDim.y;
+    const uint64_t q = (uint64_t)rt * TC_M + tid;
+    uint64_t kb = 0, dst = 0;
+    int kind = -1;
+    if (q < rows) zrow(K, a.M, t, q, a.off, kb, kind, dst);
+    float *blk = a.At + ((size_t)rt * nk + c) * 2 * 4096;
+    const float *kp = a.kap + kb;
+#pragma unroll 2
+    for (int j = 0; j < TC_KC; j += 4) {
+        const int k = c * TC_KC + j;
+        float v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (kind >= 0 && k + i < D) ? kp[k + i] : 0.f;
+        float4 h, l;
+        h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
+        h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
+        h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
+        h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
+        const uint32_t o = tc_off(tid, j) / 4;
+        *reinterpret_cast<float4 *>(blk + o) = h;
+        *reinterpret_cast<float4 *>(blk + 4096 + o) = l;
+    }
+}
+
+// Z rows of one 128-row tile x 256 samples. Thread 0 streams both operands by
+// TMA bulk copies (32 KB of A, 64 KB of W per 32-wide chunk) into two stages and
+// issues the MMAs; chunk c+1 is loaded into the stage of chunk c-1 once the MMAs
+// of chunk c-1 have completed, while those of chunk c run. All threads then read
+// the accumulator (thread i = row i) and write the rows out.
 template <int K>
 __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint64_t rows, int D) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
     uint64_t *empty = full + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 64);
+    int *flag = reinterpret_cast<int *>(smem + 2 * TC_STAGE + 128);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint64_t m0 = (uint64_t)blockIdx.x * TC_M;
-    const int sb = blockIdx.y, s0 = sb * TC_N, nsb = a.S / TC_N;
-    uint64_t kb = 0, dst = 0;
-    int kind = -1;
-    if (m0 + tid < rows) zrow(K, a.M, t, m0 + tid, a.off, kb, kind, dst);
+    const int rt = blockIdx.x, sb = blockIdx.y, s0 = sb * TC_N, nsb = a.S / TC_N;
+    const int nk = (D + TC_KC - 1) / TC_KC;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
+        *flag = 1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -529,67 +569,63 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t sbase = smem_u32(smem);
-    const int nk = (D + TC_KC - 1) / TC_KC;
-    uint32_t ph_full[2] = {0u, 0u}, ph_empty[2] = {0u, 0u};
-    bool ok = true;
-    const float *kp = a.kap + kb;
-    for (int c = 0; c < nk && ok; ++c) {
-        const int st = c & 1;
-        if (c >= 2) {  // the MMAs of chunk c-2 read this stage
-            ok = mbar_wait(&empty[st], ph_empty[st]);
-            ph_empty[st] ^= 1u;
-            if (!ok) break;
-        }
-        unsigned char *sp = smem + st * TC_STAGE;
-        if (tid == 0) tma_bulk(sp + 2 * TC_AB, a.W + ((size_t)c * nsb + sb) * 2 * 8192, 2 * TC_BB, &full[st]);
-        const int k0 = c * TC_KC;
-#pragma unroll 2
-        for (int k = 0; k < TC_KC; k += 4) {
-            float v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = (kind >= 0 && k0 + k + j < D) ? kp[k0 + k + j] : 0.f;
-            float4 h, l;
-            h.x = to_tf32(v[0]); l.x = to_tf32(v[0] - h.x);
-            h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
-            h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
-            h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
-            const uint32_t o = tc_off(tid, k);
-            *reinterpret_cast<float4 *>(sp + o) = h;
-            *reinterpret_cast<float4 *>(sp + TC_AB + o) = l;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0) {
+        const uint32_t sbase = smem_u32(smem);
+        const float *Ab = a.At + (size_t)rt * nk * 2 * 4096;
+        const float *Wb = a.W + (size_t)sb * 2 * 8192;
+        auto load = [&](int c) {
+            unsigned char *sp = smem + (c & 1) * TC_STAGE;
+            mbar_expect(&full[c & 1], 2 * TC_AB + 2 * TC_BB);
+            tma_bulk(sp, Ab + (size_t)c * 2 * 4096, 2 * TC_AB, &full[c & 1]);
+            tma_bulk(sp + 2 * TC_AB, Wb + (size_t)c * nsb * 2 * 8192, 2 * TC_BB, &full[c & 1]);
+        };
+        uint32_t ph_full[2] = {0u, 0u}, ph_empty[2] = {0u, 0u};
+        bool ok = true;
+        load(0);
+        if (nk > 1) load(1);
+        for (int c = 0; c < nk && ok; ++c) {
+            const int st = c & 1;
             ok = mbar_wait(&full[st], ph_full[st]);
             ph_full[st] ^= 1u;
-            if (ok) {
-                tc_fence_after();
-                const uint32_t sbs = sbase + st * TC_STAGE;
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sbs = sbase + st * TC_STAGE;
 #pragma unroll
-                for (int j = 0; j < TC_KC / 8; ++j) {
-                    const uint32_t o = j * 256;  // two core matrices per 8-wide slice of K
-                    const uint64_t ahi = tc_desc(sbs + o), alo = tc_desc(sbs + TC_AB + o);
-                    const uint64_t bhi = tc_desc(sbs + 2 * TC_AB + o), blo = tc_desc(sbs + 2 * TC_AB + TC_BB + o);
-                    tc_mma(tmem, ahi, bhi, (c > 0 || j > 0) ? 1u : 0u);
-                    tc_mma(tmem, ahi, blo, 1u);
-                    tc_mma(tmem, alo, bhi, 1u);
-                }
-                tc_commit(&empty[st]);
+            for (int j = 0; j < TC_KC / 8; ++j) {
+                const uint32_t o = j * 256;  // two core matrices per 8-wide slice of K
+                const uint64_t ahi = tc_desc(sbs + o), alo = tc_desc(sbs + TC_AB + o);
+                const uint64_t bhi = tc_desc(sbs + 2 * TC_AB + o), blo = tc_desc(sbs + 2 * TC_AB + TC_BB + o);
+                tc_mma(tmem, ahi, bhi, (c > 0 || j > 0) ? 1u : 0u);
+                tc_mma(tmem, ahi, blo, 1u);
+                tc_mma(tmem, alo, bhi, 1u);
+            }
+            tc_commit(&empty[st]);
+            // refill the other stage with chunk c+1 once the MMAs of chunk c-1 are done
+            if (c >= 1 && c + 1 < nk) {
+                const int so = (c + 1) & 1;
+                ok = mbar_wait(&empty[so], ph_empty[so]);
+                ph_empty[so] ^= 1u;
+                if (ok) load(c + 1);
             }
         }
-        ok = __syncthreads_and(ok);
+        // the loop waited for chunks 0 .. nk-3; wait for the last two
+        for (int c = (nk >= 2 ? nk - 2 : 0); c < nk && ok; ++c) {
+            const int st = c & 1;
+            ok = mbar_wait(&empty[st], ph_empty[st]);
+            ph_empty[st] ^= 1u;
+        }
+        if (!ok) {
+            *flag = 0;
+            if (a.status) atomicOr(a.status, ST_TIMEOUT);
+        }
     }
-    // wait for the chunks whose MMAs have not been waited for
-    for (int c = (nk >= 2 ? nk - 2 : 0); c < nk && ok; ++c) {
-        const int st = c & 1;
-        ok = mbar_wait(&empty[st], ph_empty[st]);
-        ph_empty[st] ^= 1u;
-    }
-    if (!ok) {
-        if (tid == 0 && a.status) atomicOr(a.status, ST_TIMEOUT);
-    } else {
-        tc_fence_after();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (*flag) {
+        uint64_t kb = 0, dst = 0;
+        int kind = -1;
+        if (m0 + tid < rows) zrow(K, a.M, t, m0 + tid, a.off, kb, kind, dst);
         float *out = kind == 0 ? a.G
                    : kind == 1 ? a.Z + dst * a.S
                    : kind == 2 ? a.Z5 + dst * a.S
@@ -924,6 +960,19 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
     take(L.X, K >= 4 ? cb(M, 2) : 0);
     // W: plain [r][S], or for the tensor-core product hi / lo copies of 32-padded chunks
     take(L.W, 2 * ((K >= 4 ? cb(M - 1, 2) : (size_t)M) + 32));
+    // tensor-core product rows: max over the steps of (row tiles x chunks) x 8192 floats
+    size_t at = 0;
+    if (precision != 0)
+        for (int t = 1; t <= M; ++t) {
+            const uint64_t D = K == 3 ? (uint64_t)(t - 1) : cb(t - 1, 2);
+            const uint64_t rows = K == 3   ? 1 + (uint64_t)(M - t)
+                                  : K == 4 ? 1 + 2 * (uint64_t)(M - t)
+                                           : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
+            const size_t n = (size_t)((rows + 127) / 128) * ((D + 31) / 32) * 8192;
+            if (n > at) at = n;
+        }
+    L.At = off;
+    off = a256(off + at * sizeof(float));
     take(L.CA, K >= 4 ? 3 * ((size_t)M + 1) : 0);
     take(L.T, K >= 4 ? 2 * cb(M - 1, 2) : 0);
     L.bw = off;
@@ -974,8 +1023,9 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
                                            : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
             if constexpr (sizeof(R) == 4) {
                 if (tc) {
-                    dim3 grid((unsigned)((rows + TC_M - 1) / TC_M), (unsigned)(S / TC_N));
-                    ztc_kernel<K><<<grid, 128, TC_SMEM, st>>>(a, t, rows, D);
+                    const unsigned nrt = (unsigned)((rows + TC_M - 1) / TC_M), nk = (unsigned)((D + TC_KC - 1) / TC_KC);
+                    atc_kernel<K><<<dim3(nrt, nk), 128, 0, st>>>(a, t, rows, D);
+                    ztc_kernel<K><<<dim3(nrt, (unsigned)(S / TC_N)), 128, TC_SMEM, st>>>(a, t, rows, D);
                 } else {
                     dim3 grid((unsigned)((rows + 16 * TM - 1) / (16 * TM)), (unsigned)(S / (16 * TN)));
                     zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
@@ -1027,6 +1077,7 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
     a.CB = a.CA + ((size_t)c.M + 1) * c.S;
     a.CC = a.CB + ((size_t)c.M + 1) * c.S;
     a.T = reinterpret_cast<R *>(w + L.T);
+    a.At = reinterpret_cast<float *>(w + L.At);
     a.bw = reinterpret_cast<uint32_t *>(w + L.bw);
     a.status = reinterpret_cast<unsigned *>(w);
     {

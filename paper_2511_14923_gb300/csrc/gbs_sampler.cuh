@@ -9,7 +9,7 @@ namespace smp {
 
 // Byte offsets of the per-sample arrays ([entries][S]) in the workspace.
 struct SamplerLayout {
-    size_t chi, P, Pp, P1, P2, Z, Z5, G, Y, X, W, CA, T, bw, kap, hs, H, lead, total;
+    size_t chi, P, Pp, P1, P2, Z, Z5, G, Y, X, W, CA, T, bw, kap, hs, H, lead, At, total;
 };
 SamplerLayout sampler_layout(int M, int K, int S, int precision);
 
