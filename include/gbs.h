@@ -182,7 +182,11 @@ typedef enum {
     GBS_SAMPLE_FP32 = 1  /* cumulants converted to FP32 in the workspace, as the paper stores them */
 } gbs_sample_precision;
 
-/* Workspace bytes for gbs_sample with this (M, K, batch, precision); 0 if invalid.
+/* Largest batch (samples per chunk) gbs_sample accepts. */
+#define GBS_MAX_SAMPLE_BATCH (1 << 21)
+
+/* Workspace bytes for gbs_sample with this (M, K, batch, precision); 0 if invalid
+   (batch must be a multiple of 128 in [128, GBS_MAX_SAMPLE_BATCH]).
    Grows as batch x C(M, 3) entries for K = 4, 5 (the p2 table and, for K = 5,
    the stored products), batch x C(M, 2) for K = 3. */
 size_t gbs_sampler_workspace_bytes(int M, int K, int batch, int precision);

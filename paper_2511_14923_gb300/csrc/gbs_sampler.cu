@@ -786,6 +786,57 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
     }
 }
 
+// VW consecutive samples of one lane, loaded and stored as one vector.
+template <class R, int VW>
+struct Lanes {
+    R v[VW];
+};
+template <class R, int VW>
+__device__ __forceinline__ Lanes<R, VW> ldl(const R *p) {
+    Lanes<R, VW> r;
+    if constexpr (VW == 1) {
+        r.v[0] = *p;
+    } else if constexpr (VW == 2) {
+        const auto q = *reinterpret_cast<const typename Pair2<R>::T *>(p);
+        r.v[0] = q.x;
+        r.v[1] = q.y;
+    } else {
+        static_assert(VW % 4 == 0 && sizeof(R) == 4, "four or more lanes: float only");
+#pragma unroll
+        for (int h = 0; h < VW / 4; ++h) {
+            const float4 q = reinterpret_cast<const float4 *>(p)[h];
+            r.v[4 * h] = q.x;
+            r.v[4 * h + 1] = q.y;
+            r.v[4 * h + 2] = q.z;
+            r.v[4 * h + 3] = q.w;
+        }
+    }
+    return r;
+}
+template <class R, int VW>
+__device__ __forceinline__ void stl(R *p, const R (&x)[VW]) {
+    if constexpr (VW == 1) {
+        *p = x[0];
+    } else if constexpr (VW == 2) {
+        typename Pair2<R>::T q;
+        q.x = x[0];
+        q.y = x[1];
+        *reinterpret_cast<typename Pair2<R>::T *>(p) = q;
+    } else {
+#pragma unroll
+        for (int h = 0; h < VW / 4; ++h)
+            reinterpret_cast<float4 *>(p)[h] = make_float4(x[4 * h], x[4 * h + 1], x[4 * h + 2], x[4 * h + 3]);
+    }
+}
+// Sample-independent part of the address of P2~[x][e][d] (with its boundary
+// cases P2~[x][x][d] = P1~[x-1][d], P1~[y][y] = P~[y-1]).
+template <class R>
+__device__ __forceinline__ const R *p2_row(const Args<R> &a, int x, int e, int d) {
+    const size_t S = (size_t)a.S;
+    if (e != x) return a.P2 + i_p2(x, e, d) * S;
+    return d == x - 1 ? a.P + (size_t)(x - 2) * S : a.P1 + i_p1(x - 1, d) * S;
+}
+
 // P2~[n][e][d], n-1 >= e > d >= 1 (Eq. probdoubleelidedade).
 // Order 2: i > e reaches P2~[i-1][e][d] (factor Pp~[n-1][i+1]); i < e reaches
 // P2~[e-1][max(i,d)][min(i,d)] (common factor Pp~[n-1][e+1]). The loops walk the
@@ -796,77 +847,125 @@ __global__ void __launch_bounds__(ETB) p1_kernel(Args<R> a, int n) {
 // enter P1~[n][e] with weight CA[i] kappa(d,i,n) chi_d and P1~[n][d] with weight
 // CA[i] kappa(e,i,n) chi_e. Both sums are formed here, without chi_d / chi_e, and
 // left in T for p1_kernel, so each value is read once per step.
-template <class R>
-__global__ void __launch_bounds__(ETB) p2_kernel(Args<R> a, int n) {
-    const int s = blockIdx.x * ETB + threadIdx.x;
+// Schedule: one warp (one block) per pair (e, d) and 32 VW consecutive samples,
+// VW per lane (vector loads), the samples along the slow grid axis, so that the
+// pairs of one sample group run together and the three reads of each p2 value
+// (two in the row sums over i < e, one in the column sum over i > e) fall close
+// in time and are mostly served by L2.
+template <class R, int VW>
+__global__ void __launch_bounds__(32) p2_kernel(Args<R> a, int n) {
+    const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
     const size_t S = (size_t)a.S;
     const uint64_t nr = cb(n - 1, 2);
     const R *P1 = a.P1 + s, *P2 = a.P2 + s, *P = a.P + s;
-    for (uint64_t r = blockIdx.y; r < nr; r += gridDim.y) {
+    const R *CA = a.CA + s, *CB = a.CB + s, *CC = a.CC + s;
+    R cn[VW];
+    {
+        const uint32_t *bw = a.bw + (size_t)(n >> 5) * S + s;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) cn[k] = (bw[k] >> (n & 31)) & 1u ? R(-1) : R(1);
+    }
+    const auto ld = lead(a, n);
+    for (uint64_t r = blockIdx.x; r < nr; r += gridDim.x) {
         int hi, lo;
         pair_of(r, hi, lo);
         const int e = hi + 1, d = lo + 1;
-        Spins<R> sp(a, s);
-        const R cn = sp(n);
-        R acc = R(0);
+        R acc[VW], tE[VW], tD[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = tE[k] = tD[k] = R(0);
         if (a.op2 >= 2) {
-            R t = R(0);
-            const R *CB = a.CB + s, *CC = a.CC + s;
+            R t[VW];
+#pragma unroll
+            for (int k = 0; k < VW; ++k) t[k] = R(0);
             // i < d: P2~[e-1][d][i]
             if (d < e - 1) {
                 const R *q = P2 + i_p2(e - 1, d, 1) * S;
 #pragma unroll 4
-                for (int i = 1; i < d; ++i, q += S) t = fma(CB[i * S], *q, t);
+                for (int i = 1; i < d; ++i, q += S) {
+                    const auto c = ldl<R, VW>(CB + i * S), v = ldl<R, VW>(q);
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) t[k] = fma(c.v[k], v.v[k], t[k]);
+                }
             } else {
                 const R *q = P1 + (e >= 3 ? i_p1(e - 2, 1) : 0) * S;
-                for (int i = 1; i < d; ++i, q += S) t = fma(CB[i * S], i == e - 2 ? P[(size_t)(e - 3) * S] : *q, t);
+                for (int i = 1; i < d; ++i, q += S) {
+                    const auto c = ldl<R, VW>(CB + i * S), v = ldl<R, VW>(i == e - 2 ? P + (size_t)(e - 3) * S : q);
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) t[k] = fma(c.v[k], v.v[k], t[k]);
+                }
             }
             // d < i < e: P2~[e-1][i][d]
             if (d + 1 <= e - 2) {
                 uint64_t idx = i_p2(e - 1, d + 1, d);
 #pragma unroll 4
                 for (int i = d + 1; i < e - 1; ++i) {
-                    t = fma(CB[i * S], P2[idx * S], t);
+                    const auto c = ldl<R, VW>(CB + i * S), v = ldl<R, VW>(P2 + idx * S);
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) t[k] = fma(c.v[k], v.v[k], t[k]);
                     idx += (uint64_t)(i - 1);
                 }
             }
-            if (d < e - 1) t = fma(CB[(e - 1) * S], d == e - 2 ? P[(size_t)(e - 3) * S] : P1[i_p1(e - 2, d) * S], t);
-            acc = pp(a, n - 1, e + 1, s) * t;
+            if (d < e - 1) {
+                const auto c = ldl<R, VW>(CB + (e - 1) * S);
+                const auto v = ldl<R, VW>(d == e - 2 ? P + (size_t)(e - 3) * S : P1 + i_p1(e - 2, d) * S);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) t[k] = fma(c.v[k], v.v[k], t[k]);
+            }
+            if (e + 1 > n - 1) {
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = t[k];
+            } else {
+                const auto w = ldl<R, VW>(a.Pp + i_pp(n - 1, e + 1) * S + s);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = w.v[k] * t[k];
+            }
         }
-        R tE = R(0), tD = R(0);
         if ((a.op2 >= 2 || a.op1 >= 3) && e + 1 < n) {
-            const R *CA = a.CA + s, *CC = a.CC + s;
             const R *k3n = a.kap + a.off[3] + cb(n - 1, 3) - 1;  // k3n[C(i-1,2) + j] = kappa(j, i, n)
-            R a2 = R(0);
-            // i > e: P2~[i-1][e][d] (i = e + 1: P1~[e-1][d], or P~[e-2] when d = e - 1)
+            R a2[VW];
+            // i = e + 1: P1~[e-1][d], or P~[e-2] when d = e - 1
             {
-                const R v = d == e - 1 ? P[(size_t)(e - 2) * S] : P1[i_p1(e - 1, d) * S];
+                const auto v = ldl<R, VW>(d == e - 1 ? P + (size_t)(e - 2) * S : P1 + i_p1(e - 1, d) * S);
                 const R *kp = k3n + cb(e, 2);
-                const R ca = CA[(e + 1) * S];
-                a2 = CC[(e + 1) * S] * v;
-                tE = ca * kp[d] * v;
-                tD = ca * kp[e] * v;
+                const R kd = kp[d], ke = kp[e];
+                const auto ca = ldl<R, VW>(CA + (e + 1) * S), cc = ldl<R, VW>(CC + (e + 1) * S);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    a2[k] = cc.v[k] * v.v[k];
+                    tE[k] = ca.v[k] * kd * v.v[k];
+                    tD[k] = ca.v[k] * ke * v.v[k];
+                }
             }
             uint64_t idx = i_p2(e + 1, e, d);
 #pragma unroll 4
             for (int i = e + 2; i < n; ++i) {
-                const R v = P2[idx * S];
+                const auto v = ldl<R, VW>(P2 + idx * S);
                 const R *kp = k3n + cb(i - 1, 2);
-                const R ca = CA[i * S];
-                a2 = fma(CC[i * S], v, a2);
-                tE = fma(ca * kp[d], v, tE);
-                tD = fma(ca * kp[e], v, tD);
+                const R kd = kp[d], ke = kp[e];
+                const auto ca = ldl<R, VW>(CA + i * S), cc = ldl<R, VW>(CC + i * S);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) {
+                    a2[k] = fma(cc.v[k], v.v[k], a2[k]);
+                    tE[k] = fma(ca.v[k] * kd, v.v[k], tE[k]);
+                    tD[k] = fma(ca.v[k] * ke, v.v[k], tD[k]);
+                }
                 idx += cb(i - 2, 2);
             }
-            if (a.op2 >= 2) acc += a2;
+            if (a.op2 >= 2) {
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] += a2[k];
+            }
         }
         if (a.op1 >= 3) {
             const uint64_t o = 2 * r;
-            a.T[o * S + s] = tE;
-            a.T[(o + 1) * S + s] = tD;
+            stl<R, VW>(a.T + o * S + s, tE);
+            stl<R, VW>(a.T + (o + 1) * S + s, tD);
         }
-        const auto ld = lead(a, n);
-        a.P2[i_p2(n, e, d) * S + s] = fma(cn, acc, fma(ld.x, cn, ld.y) * p2(a, n - 1, e, d, s));
+        const auto pv = ldl<R, VW>(p2_row(a, n - 1, e, d) + s);
+        R out[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) out[k] = fma(cn[k], acc[k], fma(ld.x, cn[k], ld.y) * pv.v[k]);
+        stl<R, VW>(a.P2 + i_p2(n, e, d) * S + s, out);
     }
 }
 
@@ -1040,7 +1139,11 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
         if (K >= 4 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
         if (K >= 4 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
-        if (K >= 4 && t > 2) p2_kernel<R><<<egrid(S, cb(t - 1, 2)), ETB, 0, st>>>(a, t);  // before p1: fills T
+        if (K >= 4 && t > 2) {  // before p1: fills T
+            constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // samples per lane (batch: a multiple of 128)
+            const uint64_t nr = cb(t - 1, 2);
+            p2_kernel<R, VW><<<dim3((unsigned)(nr < (1u << 30) ? nr : (1u << 30)), (unsigned)(S / (32 * VW))), 32, 0, st>>>(a, t);
+        }
         if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1153,7 +1256,7 @@ bool dev_ptr(const void *p) {
 
 bool valid_shape(int M, int K, int batch, int precision) {
     return K >= 3 && K <= 5 && M >= K && M <= (K == 3 ? GBS_MAX_MODES_K3 : GBS_MAX_MODES) && batch >= 128 &&
-           batch % 128 == 0 &&
+           batch <= GBS_MAX_SAMPLE_BATCH && batch % 128 == 0 &&
            (precision == GBS_SAMPLE_FP64 || precision == GBS_SAMPLE_FP32);
 }
 

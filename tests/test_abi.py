@@ -76,6 +76,16 @@ def test_workspace_bytes_rejects_invalid():
     assert gbs.lib().gbs_workspace_bytes(8, 3, 7) == 0
 
 
+def test_sampler_workspace_bytes_limits():
+    """Host-side shape checks of gbs_sample: K in 3..5, M >= K, batch a multiple of
+    128 up to GBS_MAX_SAMPLE_BATCH (2^21), a known precision."""
+    q = gbs.sampler_workspace_bytes
+    assert q(144, 5, 8192) > 0 and q(144, 5, 8192, "fp64") > 0
+    assert q(8, 5, 1 << 21) > 0 and q(8, 5, (1 << 21) + 128) == 0
+    assert q(8, 5, 64) == 0 and q(8, 5, 200) == 0 and q(4, 5, 128) == 0 and q(8, 6, 128) == 0
+    assert gbs.lib().gbs_sampler_workspace_bytes(8, 5, 128, 7) == 0
+
+
 def test_compute_entry_rejects_bad_arguments_without_launching():
     L = gbs.lib()
     vp = ctypes.c_void_p

@@ -129,6 +129,7 @@ def test_invalid_arguments():
     assert gbs.sampler_workspace_bytes(4, 5, 128) == 0
     assert gbs.sampler_workspace_bytes(1025, 5, 128) == 0 and gbs.sampler_workspace_bytes(1152, 3, 128) > 0
     assert gbs.sampler_workspace_bytes(8, 5, 64) == 0
+    assert gbs.sampler_workspace_bytes(8, 5, (1 << 21) + 128) == 0 and gbs.sampler_workspace_bytes(8, 5, 1 << 21) > 0
 
 
 def test_fp32_tensor_core_product_matches_simt(monkeypatch):
