@@ -851,9 +851,11 @@ __device__ __forceinline__ const R *p2_row(const Args<R> &a, int x, int e, int d
 // VW per lane (vector loads), the samples along the slow grid axis, so that the
 // pairs of one sample group run together and the three reads of each p2 value
 // (two in the row sums over i < e, one in the column sum over i > e) fall close
-// in time and are mostly served by L2.
+// in time and are mostly served by L2. The kernel is bound by load latency: the
+// bounds cap it at 64 registers, so that 32 one-warp blocks (the per-SM block
+// limit) stay resident.
 template <class R, int VW>
-__global__ void __launch_bounds__(32) p2_kernel(Args<R> a, int n) {
+__global__ void __launch_bounds__(32, 32) p2_kernel(Args<R> a, int n) {
     const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
     const size_t S = (size_t)a.S;
     const uint64_t nr = cb(n - 1, 2);
@@ -966,6 +968,119 @@ __global__ void __launch_bounds__(32) p2_kernel(Args<R> a, int n) {
 #pragma unroll
         for (int k = 0; k < VW; ++k) out[k] = fma(cn[k], acc[k], fma(ld.x, cn[k], ld.y) * pv.v[k]);
         stl<R, VW>(a.P2 + i_p2(n, e, d) * S + s, out);
+    }
+}
+
+// Spins of VW consecutive samples from their packed bits (vector loads); the
+// current 32-bit words are cached as in Spins.
+template <class R, int VW>
+struct SpinsV {
+    const uint32_t *bw;
+    size_t S;
+    int s, w;
+    uint32_t cur[VW];
+    __device__ SpinsV(const Args<R> &a, int s_) : bw(a.bw), S((size_t)a.S), s(s_), w(-1) {}
+    __device__ __forceinline__ void operator()(int v, R (&x)[VW]) {
+        if ((v >> 5) != w) {
+            w = v >> 5;
+            const uint32_t *p = bw + (size_t)w * S + s;
+            if constexpr (VW == 4) {
+                const uint4 q = *reinterpret_cast<const uint4 *>(p);
+                cur[0] = q.x;
+                cur[1] = q.y;
+                cur[2] = q.z;
+                cur[3] = q.w;
+            } else if constexpr (VW == 2) {
+                const uint2 q = *reinterpret_cast<const uint2 *>(p);
+                cur[0] = q.x;
+                cur[1] = q.y;
+            } else {
+                cur[0] = *p;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < VW; ++k) x[k] = (cur[k] >> (v & 31)) & 1u ? R(-1) : R(1);
+    }
+};
+
+// P1~[n][e] (Eq. probelidedade; K = 3: Eq. b), the same sums as p1_kernel, one
+// warp per elided variable e and 32 VW consecutive samples (VW per lane), the
+// sample groups on the slow grid axis as in p2_kernel: each p2 value of row
+// n - 1 is read by the warps of e = hi and e = lo of the same group.
+template <class R, int K, int VW>
+__global__ void __launch_bounds__(32, 32) p1v_kernel(Args<R> a, int n) {
+    const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
+    const size_t S = (size_t)a.S;
+    R cn[VW];
+    {
+        SpinsV<R, VW> sn(a, s);
+        sn(n, cn);
+    }
+    const auto ld = lead(a, n);
+    for (int e = 1 + (int)blockIdx.x; e < n; e += (int)gridDim.x) {
+        R acc[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = R(0);
+        if (a.op1 >= 2) {
+            SpinsV<R, VW> sp(a, s);
+            for (int i = 1; i < n; ++i) {
+                if (i == e) continue;
+                const int hi = i > e ? i : e, lo = i > e ? e : i;
+                R c[VW];
+                sp(i, c);
+                const R k2v = k2(a, i, n);
+                if (K == 3) {
+                    const auto q = ldl<R, VW>((lo == hi - 1 ? a.P + (size_t)(hi - 2) * S : a.P1 + i_p1(hi - 1, lo) * S) + s);
+                    if (hi + 1 > n - 1) {
+#pragma unroll
+                        for (int k = 0; k < VW; ++k) acc[k] = fma(k2v * c[k] * R(1), q.v[k], acc[k]);
+                    } else {
+                        const auto w = ldl<R, VW>(a.Pp + i_pp(n - 1, hi + 1) * S + s);
+#pragma unroll
+                        for (int k = 0; k < VW; ++k) acc[k] = fma(k2v * c[k] * w.v[k], q.v[k], acc[k]);
+                    }
+                } else {
+                    const auto q = ldl<R, VW>(p2_row(a, n - 1, hi, lo) + s);
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) acc[k] = fma(k2v * c[k], q.v[k], acc[k]);
+                }
+            }
+        }
+        if (K >= 4 && a.op1 >= 3) {
+            if (e >= 3) {
+                const auto x = ldl<R, VW>(a.X + i_z(e, n) * S + s);
+                if (e + 1 > n - 1) {
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) acc[k] = fma(R(1), x.v[k], acc[k]);
+                } else {
+                    const auto w = ldl<R, VW>(a.Pp + i_pp(n - 1, e + 1) * S + s);
+#pragma unroll
+                    for (int k = 0; k < VW; ++k) acc[k] = fma(w.v[k], x.v[k], acc[k]);
+                }
+            }
+            // pairs (e, d), d < e, carry chi_d-weighted parts for e; pairs (j, e), j > e, for e
+            const R *T = a.T + s;
+            SpinsV<R, VW> sd(a, s);
+            for (int d = 1; d < e; ++d) {
+                R c[VW];
+                sd(d, c);
+                const auto t = ldl<R, VW>(T + (2 * (cb(e - 1, 2) + (uint64_t)(d - 1))) * S);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = fma(c[k], t.v[k], acc[k]);
+            }
+            for (int j = e + 1; j < n; ++j) {
+                R c[VW];
+                sd(j, c);
+                const auto t = ldl<R, VW>(T + (2 * (cb(j - 1, 2) + (uint64_t)(e - 1)) + 1) * S);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = fma(c[k], t.v[k], acc[k]);
+            }
+        }
+        const auto pv = ldl<R, VW>((e == n - 1 ? a.P + (size_t)(n - 2) * S : a.P1 + i_p1(n - 1, e) * S) + s);
+        R out[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) out[k] = fma(cn[k], acc[k], fma(ld.x, cn[k], ld.y) * pv.v[k]);
+        stl<R, VW>(a.P1 + i_p1(n, e) * S + s, out);
     }
 }
 
@@ -1144,7 +1259,12 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
             const uint64_t nr = cb(t - 1, 2);
             p2_kernel<R, VW><<<dim3((unsigned)(nr < (1u << 30) ? nr : (1u << 30)), (unsigned)(S / (32 * VW))), 32, 0, st>>>(a, t);
         }
-        if (t > 1) p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        if (t > 1) {
+            // FP32 (large batches): warp per e over 128-sample groups; FP64 calls, whose
+            // few hundred samples give few groups, keep the (samples, entries) grid
+            if constexpr (sizeof(R) == 4) p1v_kernel<R, K, 4><<<dim3((unsigned)(t - 1), (unsigned)(S / 128)), 32, 0, st>>>(a, t);
+            else p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
