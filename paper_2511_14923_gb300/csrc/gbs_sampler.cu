@@ -1084,6 +1084,107 @@ __global__ void __launch_bounds__(32, 32) p1v_kernel(Args<R> a, int n) {
     }
 }
 
+// Pp~[x][b] of VW consecutive samples (1 when the range is empty, b > x).
+template <class R, int VW>
+__device__ __forceinline__ Lanes<R, VW> ppl(const Args<R> &a, int x, int b, int s) {
+    if (b > x) {
+        Lanes<R, VW> r;
+#pragma unroll
+        for (int k = 0; k < VW; ++k) r.v[k] = R(1);
+        return r;
+    }
+    return ldl<R, VW>(a.Pp + i_pp(x, b) * (size_t)a.S + s);
+}
+
+// FP32 forms of y_kernel, pv_kernel and pp_kernel with the schedule of p2_kernel:
+// one warp per entry and 32 VW consecutive samples (VW per lane), the sample
+// groups on the slow grid axis; the same terms in the same order per sample.
+template <class R, int VW>
+__global__ void __launch_bounds__(32, 32) yv_kernel(Args<R> a, int n) {
+    const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
+    const size_t S = (size_t)a.S;
+    for (int i = 3 + (int)blockIdx.x; i < n; i += (int)gridDim.x) {
+        SpinsV<R, VW> sp(a, s);
+        const auto z = ldl<R, VW>(a.Z + i_z(i, n) * S + s);
+        R y[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) y[k] = z.v[k];
+        for (int j = 3; j < i; ++j) {
+            R c[VW];
+            sp(j, c);
+            const auto w = ppl<R, VW>(a, i - 1, j + 1, s);
+            const auto z5 = ldl<R, VW>(a.Z5 + i_z5(j, i, n) * S + s);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) y[k] = fma(c[k] * w.v[k], z5.v[k], y[k]);
+        }
+        stl<R, VW>(a.Y + (size_t)i * S + s, y);
+    }
+}
+
+template <class R, int VW>
+__global__ void __launch_bounds__(32, 32) pvv_kernel(Args<R> a, int n) {
+    const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
+    const size_t S = (size_t)a.S;
+    for (int j = 1 + (int)blockIdx.x; j < n; j += (int)gridDim.x) {
+        SpinsV<R, VW> sp(a, s);
+        R v[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] = R(0);
+        for (int i = j + 1; i < n; ++i) {
+            R c[VW];
+            sp(i, c);
+            const R k3v = k3(a, j, i, n);
+            const auto w = ppl<R, VW>(a, n - 1, i + 1, s), q = ppl<R, VW>(a, i - 1, j + 1, s);
+#pragma unroll
+            for (int k = 0; k < VW; ++k) v[k] = fma(k3v * c[k] * w.v[k], q.v[k], v[k]);
+        }
+        R cj[VW];
+        sp(j, cj);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) v[k] = v[k] * cj[k];
+        stl<R, VW>(a.Y + (size_t)j * S + s, v);
+    }
+}
+
+template <class R, int VW>
+__global__ void __launch_bounds__(32, 32) ppv_kernel(Args<R> a, int n) {
+    const int s = (int)blockIdx.y * (32 * VW) + (int)threadIdx.x * VW;
+    const size_t S = (size_t)a.S;
+    R cn[VW];
+    {
+        SpinsV<R, VW> sn(a, s);
+        sn(n, cn);
+    }
+    const auto ld = lead(a, n);
+    for (int l = 1 + (int)blockIdx.x; l <= n; l += (int)gridDim.x) {
+        R acc[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = R(0);
+        if (a.opp >= 2) {
+            SpinsV<R, VW> sp(a, s);
+            for (int i = l; i < n; ++i) {
+                R c[VW];
+                sp(i, c);
+                const R k2v = k2(a, i, n);
+                const auto w = ppl<R, VW>(a, n - 1, i + 1, s), q = ppl<R, VW>(a, i - 1, l, s);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = fma(k2v * c[k] * w.v[k], q.v[k], acc[k]);
+            }
+        }
+        if (a.opp >= 3)
+            for (int j = l; j < n - 1; ++j) {
+                const auto y = ldl<R, VW>(a.Y + (size_t)j * S + s), q = ppl<R, VW>(a, j - 1, l, s);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) acc[k] = fma(y.v[k], q.v[k], acc[k]);
+            }
+        const auto w = ppl<R, VW>(a, n - 1, l, s);
+        R out[VW];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) out[k] = fma(cn[k], acc[k], fma(ld.x, cn[k], ld.y) * w.v[k]);
+        stl<R, VW>(a.Pp + i_pp(n, l) * S + s, out);
+    }
+}
+
 template <class R>
 __global__ void init_kernel(Args<R> a) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1249,10 +1350,21 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
                 zgemm_kernel<R, K, TM, TN><<<grid, 256, 0, st>>>(a, t, rows, D);
             }
         }
-        if (K == 5 && t > 3) y_kernel<R><<<egrid(S, (uint64_t)(t - 3)), ETB, 0, st>>>(a, t);
+        // FP32 (large batches): warp-per-entry kernels over 128-sample groups; FP64
+        // calls, a few hundred samples, keep the (samples, entries) grids
+        constexpr bool grouped = sizeof(R) == 4;
+        const unsigned gy = (unsigned)(S / 128);
+        if (K == 5 && t > 3) {
+            if constexpr (grouped) yv_kernel<R, 4><<<dim3((unsigned)(t - 3), gy), 32, 0, st>>>(a, t);
+            else y_kernel<R><<<egrid(S, (uint64_t)(t - 3)), ETB, 0, st>>>(a, t);
+        }
         bias_kernel<R, K><<<(S + TB - 1) / TB, TB, 0, st>>>(a, t);
-        if (K >= 4 && a.opp >= 3 && t > 1) pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
-        pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
+        if (K >= 4 && a.opp >= 3 && t > 1) {
+            if constexpr (grouped) pvv_kernel<R, 4><<<dim3((unsigned)(t - 1), gy), 32, 0, st>>>(a, t);
+            else pv_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
+        }
+        if constexpr (grouped) ppv_kernel<R, 4><<<dim3((unsigned)t, gy), 32, 0, st>>>(a, t);
+        else pp_kernel<R><<<egrid(S, (uint64_t)t), ETB, 0, st>>>(a, t);
         if (K >= 4 && t > 1) coef_kernel<R><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         if (K >= 4 && t > 2) {  // before p1: fills T
             constexpr int VW = sizeof(R) == 4 ? 4 : 2;  // samples per lane (batch: a multiple of 128)
@@ -1260,9 +1372,7 @@ static cudaError_t run_chunk(Args<R> a, double *prob, cudaStream_t st) {
             p2_kernel<R, VW><<<dim3((unsigned)(nr < (1u << 30) ? nr : (1u << 30)), (unsigned)(S / (32 * VW))), 32, 0, st>>>(a, t);
         }
         if (t > 1) {
-            // FP32 (large batches): warp per e over 128-sample groups; FP64 calls, whose
-            // few hundred samples give few groups, keep the (samples, entries) grid
-            if constexpr (sizeof(R) == 4) p1v_kernel<R, K, 4><<<dim3((unsigned)(t - 1), (unsigned)(S / 128)), 32, 0, st>>>(a, t);
+            if constexpr (grouped) p1v_kernel<R, K, 4><<<dim3((unsigned)(t - 1), gy), 32, 0, st>>>(a, t);
             else p1_kernel<R, K><<<egrid(S, (uint64_t)(t - 1)), ETB, 0, st>>>(a, t);
         }
         cudaError_t e = cudaGetLastError();
