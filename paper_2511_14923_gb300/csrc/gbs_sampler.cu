@@ -50,7 +50,10 @@
 // (1/2 if both are <= 0); P[n] keeps the chosen branch unclipped.
 //
 // Layout. Every per-sample array is [entry][S] (sample index fastest), so a warp
-// always touches 32 consecutive samples of one entry.
+// always touches consecutive samples of one entry: 32 with one sample per lane,
+// 128 in the FP32 table updates, whose lanes hold 4 samples each (16-byte loads)
+// and whose warps take one entry of one 128-sample group, the groups along the
+// slow grid axis (all entries of a group in flight together share its rows in L2).
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -701,7 +704,9 @@ __global__ void bias_kernel(Args<R> a, int n) {
 
 // ---------------------------------------------------------------- step n: table rows
 // Thread per (entry, sample); the entry comes from blockIdx.y, so every index
-// below is uniform across a warp.
+// below is uniform across a warp. These grids serve the FP64 calls (a few
+// hundred samples); FP32 runs the grouped forms further down (p2_kernel for
+// both, ppv/pvv/yv/p1v for FP32).
 
 // Order-3 part of the p+ update, factored: the term
 //   sum_{i > j >= l} kappa(j,i,n) chi_i chi_j chi_n Pp~[n-1][i+1] Pp~[i-1][j+1] Pp~[j-1][l]
