@@ -126,7 +126,10 @@ class Workspace:
         n = workspace_bytes(M, kmax, precision)
         if n == 0:
             raise GbsError(1, f"invalid (M={M}, kmax={kmax}, precision={precision})")
-        self.buf = torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+        dev = torch.device(device or "cuda")
+        if dev.type != "cuda":
+            raise TypeError("the workspace lives in device memory (a CUDA device)")
+        self.buf = torch.empty(n, dtype=torch.uint8, device=dev)
         self.nbytes = n
 
     @property
@@ -136,6 +139,41 @@ class Workspace:
     def status(self, stream=None) -> int:
         st = stream or torch.cuda.current_stream(self.buf.device)
         return int(lib().gbs_stream_status(ctypes.c_void_p(self.ptr), ctypes.c_void_p(st.cuda_stream)))
+
+
+def _workspace_for(workspace, M: int, kmax: int, precision: str, device) -> Workspace:
+    """The caller's Workspace after checking that it sits on the inputs' device and
+    is large enough for (M, kmax, precision), or a new one."""
+    if workspace is None:
+        return Workspace(M, kmax, precision, device=device)
+    if not isinstance(workspace, Workspace):
+        raise TypeError("workspace must be a Workspace")
+    if workspace.buf.device != torch.device(device):
+        raise ValueError(f"workspace is on {workspace.buf.device}, the inputs on {device}")
+    need = workspace_bytes(M, kmax, precision)
+    if workspace.nbytes < need:
+        raise GbsError(5, f"workspace holds {workspace.nbytes} bytes, (M={M}, kmax={kmax}, {precision}) needs {need}")
+    return workspace
+
+
+def _workspace_tensor(workspace, need: int, device) -> torch.Tensor:
+    """A raw device workspace: the caller's contiguous CUDA tensor on the inputs'
+    device with at least need bytes, or a new uint8 tensor."""
+    if workspace is None:
+        return torch.empty(need, dtype=torch.uint8, device=device)
+    if not isinstance(workspace, torch.Tensor) or not workspace.is_cuda:
+        raise TypeError("workspace must be a CUDA tensor")
+    if workspace.device != torch.device(device):
+        raise ValueError(f"workspace is on {workspace.device}, the inputs on {device}")
+    if not workspace.is_contiguous():
+        raise ValueError("workspace must be contiguous")
+    if _nbytes(workspace) < need:
+        raise GbsError(5, f"workspace holds {_nbytes(workspace)} bytes, {need} needed")
+    return workspace
+
+
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
 
 
 def _prep(V: torch.Tensor):
@@ -155,7 +193,7 @@ def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, worksp
         out = torch.empty(n, dtype=torch.float64, device=V.device)
     elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
-    ws = workspace or Workspace(M, kmax, precision, device=V.device)
+    ws = _workspace_for(workspace, M, kmax, precision, V.device)
     st = torch.cuda.current_stream(V.device)
     f = getattr(lib(), fname)
     _check(f(ctypes.c_void_p(V.data_ptr()), M, kmax, ctypes.c_void_p(out.data_ptr()), PRECISIONS[precision],
@@ -209,7 +247,7 @@ def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, che
         out = torch.empty(n, dtype=torch.float64, device=V.device)
     elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
-    ws = workspace or Workspace(M, kmax, "fp64", device=V.device)
+    ws = _workspace_for(workspace, M, kmax, "fp64", V.device)
     st = torch.cuda.current_stream(V.device)
     _check(lib().gbs_displaced_tables(_vp(V), _vp(mean), M, kmax, TABLES[table], _vp(out), ctypes.c_void_p(ws.ptr),
                                       ws.nbytes, ctypes.c_void_p(st.cuda_stream)))
@@ -254,13 +292,13 @@ def sample(kappa, M: int, K: int, u=None, force=None, orders=None, batch: int = 
     nb = sampler_workspace_bytes(M, K, batch, precision)
     if nb == 0:
         raise GbsError(1, f"invalid sampler shape (M={M}, K={K}, batch={batch}, precision={precision})")
-    ws = workspace if workspace is not None else torch.empty(nb, dtype=torch.uint8, device=dev)
+    ws = _workspace_tensor(workspace, nb, dev)
     ordv = None if orders is None else (ctypes.c_int * 3)(*[int(o) for o in orders])
     st = torch.cuda.current_stream(dev)
     _check(lib().gbs_sample(_vp(kappa), M, K, ordv, n, None if u is None else _vp(u),
                             None if force is None else _vp(force), _vp(bits), _vp(prob),
                             None if q0 is None else _vp(q0), batch, SAMPLE_PRECISIONS[precision], _vp(ws),
-                            ws.numel(), ctypes.c_void_p(st.cuda_stream)))
+                            _nbytes(ws), ctypes.c_void_p(st.cuda_stream)))
     if check:
         torch.cuda.synchronize(dev)
     return bits, prob, q0
@@ -284,10 +322,10 @@ def cumulants_backward(V, kmax, grad_kappa, workspace: torch.Tensor | None = Non
     if g.numel() != n:
         raise ValueError(f"grad_kappa must have {n} entries")
     nb = int(lib().gbs_backward_workspace_bytes(M, kmax))
-    ws = workspace if workspace is not None else torch.empty(nb, dtype=torch.uint8, device=V.device)
+    ws = _workspace_tensor(workspace, nb, V.device)
     out = torch.empty_like(V)
     st = torch.cuda.current_stream(V.device)
-    _check(lib().gbs_cumulants_backward(_vp(V), M, kmax, _vp(g), _vp(out), _vp(ws), ws.numel(),
+    _check(lib().gbs_cumulants_backward(_vp(V), M, kmax, _vp(g), _vp(out), _vp(ws), _nbytes(ws),
                                         ctypes.c_void_p(st.cuda_stream)))
     if check:
         _check(lib().gbs_stream_status(_vp(ws), ctypes.c_void_p(st.cuda_stream)))
@@ -422,7 +460,7 @@ def autotune(V, kmax, precision="fp32r", workspace=None) -> float:
     """Tune the prefix-tree schedule for this shape (see gbs_autotune); returns the best ms."""
     V, M = _prep(V)
     out = torch.empty(table_size(M, kmax), dtype=torch.float64, device=V.device)
-    ws = workspace or Workspace(M, kmax, precision, device=V.device)
+    ws = _workspace_for(workspace, M, kmax, precision, V.device)
     st = torch.cuda.current_stream(V.device)
     ms = ctypes.c_float(0.0)
     _check(lib().gbs_autotune(_vp(V), M, kmax, _vp(out), PRECISIONS[precision], ctypes.c_void_p(ws.ptr), ws.nbytes,

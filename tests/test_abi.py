@@ -112,3 +112,29 @@ def test_large_mode_counts_for_low_orders():
         assert gbs.unrank(r, d) == [int(c) for c in S]
     assert gbs.rank([4096]) == 2 ** 64 - 1
     assert gbs.lib().gbs_backward_workspace_bytes(1152, 3) == 0
+
+
+def test_python_workspace_checks_run_before_any_library_call():
+    """The binding rejects host-memory workspaces, foreign objects and undersized
+    workspaces on the host (GBS_ERR_WORKSPACE = 5 for the size, as the library
+    would), so no host pointer ever reaches a kernel."""
+    import torch
+    cuda0 = torch.device("cuda", 0)
+    with pytest.raises(TypeError):
+        gbs.Workspace(8, 3, device="cpu")
+    with pytest.raises(TypeError):
+        gbs._workspace_tensor(torch.empty(64, dtype=torch.uint8), 64, cuda0)
+    with pytest.raises(TypeError):
+        gbs._workspace_for(torch.empty(64, dtype=torch.uint8), 8, 3, "fp64", cuda0)
+    # a Workspace whose buffer is on another device than the inputs
+    ws = object.__new__(gbs.Workspace)
+    ws.buf, ws.nbytes = torch.empty(16, dtype=torch.uint8, device="meta"), 16
+    with pytest.raises(ValueError):
+        gbs._workspace_for(ws, 8, 3, "fp64", cuda0)
+    # same device, too small
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs._workspace_for(ws, 8, 3, "fp64", torch.device("meta"))
+    assert ei.value.code == 5
+    ws.nbytes = gbs.workspace_bytes(8, 3, "fp64")
+    assert gbs._workspace_for(ws, 8, 3, "fp64", torch.device("meta")) is ws
+    assert gbs._nbytes(torch.empty(3, dtype=torch.float64)) == 24
