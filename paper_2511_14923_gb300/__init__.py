@@ -172,6 +172,12 @@ def _workspace_tensor(workspace, need: int, device) -> torch.Tensor:
     return workspace
 
 
+def _on(t: torch.Tensor, device, name: str) -> torch.Tensor:
+    if t.device != torch.device(device):
+        raise ValueError(f"{name} is on {t.device}, the other inputs on {device}")
+    return t
+
+
 def _nbytes(t: torch.Tensor) -> int:
     return t.numel() * t.element_size()
 
@@ -193,6 +199,7 @@ def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, worksp
         out = torch.empty(n, dtype=torch.float64, device=V.device)
     elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
+    _on(out, V.device, "out")
     ws = _workspace_for(workspace, M, kmax, precision, V.device)
     st = torch.cuda.current_stream(V.device)
     f = getattr(lib(), fname)
@@ -237,7 +244,7 @@ def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, che
     V, M = _prep(V)
     if table not in TABLES:
         raise ValueError(f"table must be one of {sorted(TABLES)}")
-    mean = _dev64(mean, "mean")
+    mean = _on(_dev64(mean, "mean"), V.device, "mean")
     if mean.numel() != 2 * M:
         raise ValueError(f"mean must have 2M = {2 * M} entries")
     n = table_size(M, kmax)
@@ -247,6 +254,7 @@ def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, che
         out = torch.empty(n, dtype=torch.float64, device=V.device)
     elif out.numel() != n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
         raise ValueError(f"out must be a contiguous CUDA float64 tensor of {n} entries")
+    _on(out, V.device, "out")
     ws = _workspace_for(workspace, M, kmax, "fp64", V.device)
     st = torch.cuda.current_stream(V.device)
     _check(lib().gbs_displaced_tables(_vp(V), _vp(mean), M, kmax, TABLES[table], _vp(out), ctypes.c_void_p(ws.ptr),
@@ -277,15 +285,17 @@ def sample(kappa, M: int, K: int, u=None, force=None, orders=None, batch: int = 
     if src is None:
         raise ValueError("give u or force")
     n = src.shape[0]
+    dev = kappa.device
     if u is not None:
-        u = _dev64(u, "u")
+        u = _on(_dev64(u, "u"), dev, "u")
         if tuple(u.shape) != (n, M):
             raise ValueError("u must be (n, M)")
     if force is not None:
         if not isinstance(force, torch.Tensor) or not force.is_cuda or force.dtype != torch.uint8:
             raise TypeError("force must be a CUDA uint8 tensor")
-        force = force.contiguous()
-    dev = kappa.device
+        if tuple(force.shape) != (n, M):
+            raise ValueError("force must be (n, M)")
+        force = _on(force, dev, "force").contiguous()
     bits = torch.empty((n, M), dtype=torch.uint8, device=dev)
     prob = torch.empty(n, dtype=torch.float64, device=dev)
     q0 = torch.empty((n, M), dtype=torch.float64, device=dev) if want_q0 else None
@@ -317,7 +327,7 @@ def _dev64(t: torch.Tensor, name: str) -> torch.Tensor:
 def cumulants_backward(V, kmax, grad_kappa, workspace: torch.Tensor | None = None, check=True):
     """dL/dV (2M x 2M, symmetric) from dL/dkt (table layout), FP64."""
     V, M = _prep(V)
-    g = _dev64(grad_kappa, "grad_kappa")
+    g = _on(_dev64(grad_kappa, "grad_kappa"), V.device, "grad_kappa")
     n = table_size(M, kmax)
     if g.numel() != n:
         raise ValueError(f"grad_kappa must have {n} entries")

@@ -138,3 +138,8 @@ def test_python_workspace_checks_run_before_any_library_call():
     ws.nbytes = gbs.workspace_bytes(8, 3, "fp64")
     assert gbs._workspace_for(ws, 8, 3, "fp64", torch.device("meta")) is ws
     assert gbs._nbytes(torch.empty(3, dtype=torch.float64)) == 24
+    # inputs on different devices are refused
+    t = torch.empty(4)
+    assert gbs._on(t, torch.device("cpu"), "t") is t
+    with pytest.raises(ValueError):
+        gbs._on(t, torch.device("meta"), "t")
