@@ -1510,8 +1510,8 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
     using gbs::record_error;
     if (!valid_shape(M, K, batch, precision))
         return record_error(GBS_ERR_INVALID_ARG,
-                            "need K in {3, 4, 5}, K <= M <= 1024 (4096 for K = 3), batch a positive multiple of 128 and precision "
-                            "GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
+                            "need K in {3, 4, 5}, K <= M <= 1024 (4096 for K = 3), batch a multiple of 128 in "
+                            "[128, GBS_MAX_SAMPLE_BATCH] and precision GBS_SAMPLE_FP64 or GBS_SAMPLE_FP32");
     if (n_samples < 0) return record_error(GBS_ERR_INVALID_ARG, "n_samples must be >= 0");
     int ord[3] = {3, 3, 2};  // K = 5; K = 4: one order lower, as the paper's rule gives
     if (K == 4) ord[0] = ord[1] = 2, ord[2] = 1;
