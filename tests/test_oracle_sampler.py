@@ -10,7 +10,9 @@ the paper's expansion and by exact distributions, independent of the oracle:
   blocks of <= K modes give the exact product distribution at any M;
 * the terms beyond the first are odd in the drawn bit, so the estimated
   probabilities of all 2^M bitstrings sum to 1;
-* drawing with seeded uniforms reproduces the exact distribution's frequencies.
+* drawing with seeded uniforms reproduces the exact distribution's frequencies;
+* the same exactness holds for displaced states, whose exact click distribution
+  follows from their vacuum probabilities by inclusion-exclusion.
 """
 import itertools
 
@@ -69,6 +71,68 @@ def test_exact_for_small_M(K):
     bits = all_bits(K)
     _, p, _ = oracle.sample(kappa_table(inst.V, K), K, K, force=bits)
     np.testing.assert_allclose(p, tor_probs_of(bits, inst.V), rtol=1e-10, atol=1e-14)
+
+
+def exact_click_probs_displaced(V, mean, M):
+    """All 2^M click probabilities of a displaced state by inclusion-exclusion over
+    its vacuum probabilities: with Z the silent modes of x and C the clicking ones,
+    p(x) = sum_{T subset of C} (-1)^{|T|} P0(Z + T), P0(empty) = 1."""
+    cache = {}
+
+    def P0(S):
+        S = tuple(sorted(S))
+        if not S:
+            return 1.0
+        if S not in cache:
+            cache[S] = oracle.p0_displaced(V, mean, np.array(S))
+        return cache[S]
+
+    bits = all_bits(M)
+    out = np.empty(len(bits))
+    for r, x in enumerate(bits):
+        Z = [k for k in range(M) if not x[k]]
+        C = [k for k in range(M) if x[k]]
+        out[r] = sum((-1) ** j * P0(Z + list(T)) for j in range(len(C) + 1) for T in itertools.combinations(C, j))
+    return bits, out
+
+
+@pytest.mark.parametrize("K", [3, 4, 5])
+def test_exact_for_small_M_displaced(K):
+    """A displaced state (first moments from coherent inputs): at M = K the sampler
+    fed with the spin cumulants of its displaced tables reproduces the exact click
+    distribution of the state."""
+    inst = synthetic.random_instance(K, K, seed=400 + K, r_range=(0.5, 1.2))
+    mean = synthetic.displaced_mean(inst, seed=40 + K, alpha_scale=0.8)
+    kap = oracle.spin_tables_displaced(inst.V, mean, K)[1]
+    bits, want = exact_click_probs_displaced(inst.V, mean, K)
+    assert abs(want.sum() - 1.0) < 1e-12 and want.min() > -1e-15
+    _, p, _ = oracle.sample(kap, K, K, force=bits)
+    np.testing.assert_allclose(p, want, rtol=1e-10, atol=1e-14)
+
+
+def test_exact_for_independent_displaced_blocks():
+    """Independent displaced blocks of <= K consecutive modes: the K = 5 sampler
+    gives the product of the blocks' exact click distributions."""
+    rng = np.random.default_rng(515)
+    sizes = (4, 5, 2)
+    insts = [synthetic.random_instance(m, 1, seed=int(rng.integers(1 << 30)), r_range=(0.5, 1.2)) for m in sizes]
+    means = [synthetic.displaced_mean(x, seed=int(rng.integers(1 << 30)), alpha_scale=0.7) for x in insts]
+    V = block_covariance([x.V for x in insts])
+    M = V.shape[0] // 2
+    mean = np.concatenate([np.concatenate([m[:x.M] for m, x in zip(means, insts)]),
+                           np.concatenate([m[x.M:] for m, x in zip(means, insts)])])
+    kap = oracle.spin_tables_displaced(V, mean, 5)[1]
+    bits = rng.integers(0, 2, (48, M)).astype(np.uint8)
+    _, p, _ = oracle.sample(kap, M, 5, force=bits)
+    want = np.ones(len(bits))
+    o = 0
+    for x, m in zip(insts, means):
+        bb, pb = exact_click_probs_displaced(x.V, m, x.M)
+        idx = (bits[:, o:o + x.M].astype(np.int64) << np.arange(x.M)).sum(axis=1)
+        lookup = dict(zip((bb.astype(np.int64) << np.arange(x.M)).sum(axis=1), pb))
+        want *= np.array([lookup[i] for i in idx])
+        o += x.M
+    np.testing.assert_allclose(p, want, rtol=1e-9)
 
 
 @pytest.mark.parametrize("K,sizes", [(3, (3, 2, 3, 1)), (4, (4, 3, 4)), (5, (5, 2, 4))])
