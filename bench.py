@@ -261,7 +261,8 @@ def bench_batch(args):
     insts = synthetic.batch_instances(256)
     N = sum(gbs.table_size(x.M, x.kmax) for x in insts)
     Vs = [torch.from_numpy(x.V).cuda() for x in insts]
-    b = gbs.Batch(Vs, [x.kmax for x in insts], args.precision)
+    # untimed: the batch autotuner picks the batched kernel's schedule for this batch
+    b = gbs.Batch(Vs, [x.kmax for x in insts], args.precision, autotune=not args.no_autotune)
     b.capture()
     for _ in range(max(args.warmup - 1, 0)):
         b.replay()
@@ -298,6 +299,7 @@ def bench_batch(args):
             "config": {"workload": "256 instances, M~U{16..144}, kmax~U{2..5}, r~U[0.5,1.5] on the first M/2 modes, "
                                    "eta_i~U[0.2,0.6], seed 20251118", "subsets": N, "table_bytes": N * 8,
                        "launch": "one persistent cooperative kernel, CUDA-graph replay", "precision": args.precision},
+            "schedule": b.schedule(), "autotune_best_ms": b.tune_ms,
             "per_instance_fp64": {"ms_per_step": ms_single, "value": N / (ms_single * 1e-3), "launches": 6 * len(insts)}}
     print(json.dumps(line), flush=True)
 

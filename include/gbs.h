@@ -55,7 +55,7 @@ typedef enum {
     GBS_ERR_INVALID_ARG = 1,  /* bad M, kmax, precision, null or misaligned pointer */
     GBS_ERR_NOT_POSDEF = 2,   /* some (V_T + I)/2 is not positive definite (device) */
     GBS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
-    GBS_ERR_TIMEOUT = 4,      /* a bounded device wait gave up (batched launch) */
+    GBS_ERR_TIMEOUT = 4,      /* a bounded device wait of the sampler (gbs_sample) gave up */
     GBS_ERR_WORKSPACE = 5     /* workspace smaller than gbs_workspace_bytes() */
 } gbs_status;
 
@@ -252,11 +252,16 @@ size_t gbs_batched_workspace_bytes(const gbs_instance *inst, int n, int precisio
 
 /* Writes the batch plan into the workspace: instance order (largest M first),
    per-instance packing buffers and lower-order P0 tables, per-phase work prefix
-   sums, and the prefix-tree item tables. inst is a HOST array; the pointers in it
-   are device pointers that must stay valid while the plan is used. Copies the
-   plan with a host-to-device copy and synchronises cuda_stream: call it outside
-   any stream capture. Returns GBS_OK, GBS_ERR_INVALID_ARG, GBS_ERR_WORKSPACE or
-   GBS_ERR_CUDA. */
+   sums, and the prefix-tree item tables, for one schedule of the batched kernel
+   (CTA shape, items per CTA, children per shared-memory batch). The schedule is
+   the one gbs_batched_autotune recorded for a batch with the same multiset of
+   (M, kmax) on this device (also read from GBS_AUTOTUNE_CACHE), else a default
+   (256 threads x 3 CTAs per SM for GBS_FP32_REFINED and 256 x 2 for GBS_FP64
+   when every M <= 577; 512 x 1 otherwise). inst is a HOST array; the pointers
+   in it are device pointers that must stay valid while the plan is used. Copies
+   the plan with a host-to-device copy and synchronises cuda_stream: call it
+   outside any stream capture. Returns GBS_OK, GBS_ERR_INVALID_ARG,
+   GBS_ERR_WORKSPACE or GBS_ERR_CUDA. */
 int gbs_batched_plan(const gbs_instance *inst, int n, int precision, void *workspace, size_t ws_bytes,
                      void *cuda_stream);
 
@@ -265,9 +270,33 @@ int gbs_batched_plan(const gbs_instance *inst, int n, int precision, void *works
    separated by grid-wide barriers; prefix-tree items of all instances share one
    queue per order). Reads V from the device pointers recorded by the plan, so it
    may be captured in a CUDA graph and replayed after V changes in place.
-   precision must equal the plan's. Asynchronous; device errors go to the status
-   word (gbs_stream_status). */
+   precision must equal the plan's, and the workspace must hold a plan written by
+   gbs_batched_plan or gbs_batched_autotune in this process (GBS_ERR_INVALID_ARG
+   otherwise). Asynchronous; device errors go to the status word
+   (gbs_stream_status). The grid-wide barriers are those of a cooperative launch,
+   whose CTAs are all resident; they carry no time limit. */
 int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream);
+
+/* Batch autotuner (the schedule search of gbs_autotune, for a ragged batch):
+   times gbs_cumulants_batched on this batch under candidate schedules -- every
+   CTA shape allowed for the precision and the largest M (512 x 1, 256 x 2 when
+   M <= 577; refined also 640 x 1 and 256 x 3 when M <= 577) at the default
+   grain and batch size, then items per CTA slot (1, 2, 4, 8) x children per
+   batch (16, 64) for the fastest shape -- records the fastest for this batch
+   shape (multiset of (M, kmax), device, precision; persisted like gbs_autotune's
+   table) and leaves its plan in the workspace, ready for gbs_cumulants_batched.
+   Arguments as for gbs_batched_plan; the outputs are overwritten with the tables.
+   Synchronises cuda_stream (not capturable). best_ms_out (host, may be NULL)
+   receives the best time in ms. Schedules never change the arithmetic. */
+int gbs_batched_autotune(const gbs_instance *inst, int n, int precision, void *workspace, size_t ws_bytes,
+                         void *cuda_stream, float *best_ms_out);
+
+/* Schedule of the batch plan in this workspace (written by gbs_batched_plan or
+   gbs_batched_autotune in this process): schedule_out[5] (host) = {CTA shape
+   (0: 512 threads x 1 per SM, 1: 256 x 2, 2: 640 x 1, 3: 256 x 3), threads per
+   CTA, CTAs in the launch, items per CTA slot, children per shared-memory
+   batch}. Returns GBS_OK or GBS_ERR_INVALID_ARG (no plan). */
+int gbs_batched_schedule(const void *workspace, int *schedule_out);
 
 /* ---------------------------------------------------------------- gradients */
 

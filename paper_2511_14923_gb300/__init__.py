@@ -77,6 +77,9 @@ def lib() -> ctypes.CDLL:
     L.gbs_batched_workspace_bytes.restype = sz
     L.gbs_batched_plan.argtypes = [ctypes.POINTER(_Instance), i32, i32, vp, sz, vp]; L.gbs_batched_plan.restype = i32
     L.gbs_cumulants_batched.argtypes = [i32, vp, vp]; L.gbs_cumulants_batched.restype = i32
+    L.gbs_batched_autotune.argtypes = [ctypes.POINTER(_Instance), i32, i32, vp, sz, vp, ctypes.POINTER(ctypes.c_float)]
+    L.gbs_batched_autotune.restype = i32
+    L.gbs_batched_schedule.argtypes = [vp, ctypes.POINTER(i32)]; L.gbs_batched_schedule.restype = i32
     for name in ("gbs_vacuum_probs", "gbs_click_moments", "gbs_cumulants", "gbs_spin_correlators",
                  "gbs_spin_cumulants"):
         f = getattr(L, name)
@@ -408,9 +411,11 @@ class Batch:
 
     Vs: list of CUDA float64 2M x 2M covariances (kept by reference: update them
     in place and call run() again, or replay the captured graph); kmaxes: list of
-    orders. outputs[i] receives instance i's table."""
+    orders. outputs[i] receives instance i's table. autotune=True times the
+    candidate schedules of the batched kernel on this batch (gbs_batched_autotune)
+    and keeps the fastest; tune_ms then holds its time."""
 
-    def __init__(self, Vs, kmaxes, precision="fp32r"):
+    def __init__(self, Vs, kmaxes, precision="fp32r", autotune=False):
         self.Vs = [_prep(V)[0] for V in Vs]
         self.kmaxes = [int(k) for k in kmaxes]
         self.precision = precision
@@ -434,6 +439,27 @@ class Batch:
         _check(lib().gbs_batched_plan(arr, len(arr), PRECISIONS[precision], _vp(self.ws), nb,
                                       ctypes.c_void_p(st.cuda_stream)))
         self.graph = None
+        self.tune_ms = None
+        if autotune:
+            self.autotune()
+
+    def autotune(self) -> float:
+        """Pick the batched kernel's schedule for this batch by timing the candidates
+        (outputs are overwritten); the plan in the workspace then uses it."""
+        st = torch.cuda.current_stream(self.ws.device)
+        ms = ctypes.c_float(0.0)
+        _check(lib().gbs_batched_autotune(self._arr, len(self._arr), PRECISIONS[self.precision], _vp(self.ws),
+                                          _nbytes(self.ws), ctypes.c_void_p(st.cuda_stream), ctypes.byref(ms)))
+        self.graph = None
+        self.tune_ms = float(ms.value)
+        return self.tune_ms
+
+    def schedule(self) -> dict:
+        """The batched kernel's schedule in this plan (gbs_batched_schedule)."""
+        arr = (ctypes.c_int * 5)()
+        _check(lib().gbs_batched_schedule(_vp(self.ws), arr))
+        shape = {0: "512x1", 1: "256x2", 2: "640x1", 3: "256x3"}.get(arr[0], str(arr[0]))
+        return {"cta_shape": shape, "threads": arr[1], "ctas": arr[2], "grain": arr[3], "children_per_batch": arr[4]}
 
     def run(self, check=False):
         st = torch.cuda.current_stream(self.ws.device)

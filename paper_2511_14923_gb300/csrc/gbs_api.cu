@@ -319,11 +319,43 @@ int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream) {
         return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
     if (!workspace || ((uintptr_t)workspace & 255))
         return fail(GBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned device memory");
+    bool planned = false;
+    cudaError_t e = gbs::launch_batched(static_cast<char *>(workspace), precision,
+                                        static_cast<cudaStream_t>(cuda_stream), planned);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    if (!planned)
+        return fail(GBS_ERR_INVALID_ARG,
+                    "the workspace holds no batch plan of this precision: call gbs_batched_plan first");
+    return ok();
+}
+
+int gbs_batched_schedule(const void *workspace, int *schedule_out) {
+    if (!workspace || !schedule_out) return fail(GBS_ERR_INVALID_ARG, "NULL workspace or output");
+    if (!gbs::batched_schedule(workspace, schedule_out))
+        return fail(GBS_ERR_INVALID_ARG, "the workspace holds no batch plan: call gbs_batched_plan first");
+    return ok();
+}
+
+int gbs_batched_autotune(const gbs_instance *inst, int n, int precision, void *workspace, size_t ws_bytes,
+                         void *cuda_stream, float *best_ms_out) {
+    int rc = check_batch(inst, n, precision);
+    if (rc != GBS_OK) return rc;
+    if (!workspace || ((uintptr_t)workspace & 255) || !is_device_ptr(workspace))
+        return fail(GBS_ERR_INVALID_ARG, "workspace must be 256-byte aligned device memory");
+    for (int i = 0; i < n; ++i)
+        if (!is_device_ptr(inst[i].V) || !is_device_ptr(inst[i].kappa_out))
+            return fail(GBS_ERR_INVALID_ARG, "instance %d: V and kappa_out must be device memory", i);
     const int sms = device_sms();
     if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
-    cudaError_t e = gbs::launch_batched(static_cast<char *>(workspace), precision, sms,
-                                        static_cast<cudaStream_t>(cuda_stream));
-    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    const size_t need = gbs::batched_workspace_bytes(inst, n, precision, sms);
+    if (ws_bytes < need) return fail(GBS_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
+    gbs::TreeCfg best;
+    float ms = 0.f;
+    int tried = 0;
+    rc = gbs::batched_autotune(inst, n, precision, static_cast<char *>(workspace), ws_bytes, sms,
+                               static_cast<cudaStream_t>(cuda_stream), best, ms, tried);
+    if (rc != GBS_OK) return fail(rc, "batched autotuning failed");
+    if (best_ms_out) *best_ms_out = ms;
     return ok();
 }
 

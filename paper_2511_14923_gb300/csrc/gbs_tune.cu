@@ -9,8 +9,13 @@
 // Results live in a process-wide table consulted by every forward call; if the
 // environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
 // it on first use and rewritten after each tuning run (a JSON array of objects).
+// Ragged batches (gbs_batched_autotune) have a second table keyed by the batch's
+// multiset of (M, kmax), hashed; its entries share the JSON file and carry a
+// "batch" key instead of "M".
 // The schedule changes only the order in which entries are computed, never their
 // arithmetic, so tuned and untuned calls return identical tables.
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -35,9 +40,49 @@ struct Entry {
     float ms;
 };
 
+using BKey = std::tuple<int, int, int, uint64_t>;  // cc, sms, precision, batch signature
+struct BEntry {
+    TreeCfg cfg;
+    float ms;
+    int n;
+};
+
 std::mutex g_mu;
 std::map<Key, Entry> g_table;
+std::map<BKey, BEntry> g_btable;
 bool g_loaded = false;
+
+// FNV-1a over the (M, kmax) pairs in sorted order, then n: the batch's shape
+// regardless of instance order.
+uint64_t batch_signature(const gbs_instance *inst, int n) {
+    std::vector<std::pair<int, int>> mk(n);
+    for (int i = 0; i < n; ++i) mk[i] = {inst[i].M, inst[i].kmax};
+    std::sort(mk.begin(), mk.end());
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint32_t v) {
+        for (int b = 0; b < 4; ++b) {
+            h ^= (v >> (8 * b)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    for (const auto &p : mk) {
+        mix((uint32_t)p.first);
+        mix((uint32_t)p.second);
+    }
+    mix((uint32_t)n);
+    return h;
+}
+
+int read_hex(const char *obj, const char *end, const char *key, uint64_t &out) {
+    char pat[32];
+    snprintf(pat, sizeof pat, "\"%s\"", key);
+    const char *p = strstr(obj, pat);
+    if (!p || p > end) return 0;
+    p = strchr(p + strlen(pat), '"');
+    if (!p || p > end) return 0;
+    out = strtoull(p + 1, nullptr, 16);
+    return 1;
+}
 
 int read_int(const char *obj, const char *end, const char *key, int &out) {
     char pat[32];
@@ -66,8 +111,15 @@ void load_locked() {
     while ((p = strchr(p, '{')) != nullptr) {
         const char *end = strchr(p, '}');
         if (!end) break;
-        int cc, sms, M, kmax, prec, grain, ccap, variant;
-        if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "M", M) &&
+        int cc, sms, M, kmax, prec, grain, ccap, variant, nb;
+        uint64_t sig;
+        if (read_hex(p, end, "batch", sig)) {
+            if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "precision", prec) &&
+                read_int(p, end, "n", nb) && read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
+                read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
+                variant >= 0 && variant <= 3)
+                g_btable[BKey{cc, sms, prec, sig}] = BEntry{TreeCfg{grain, ccap, variant}, -1.f, nb};
+        } else if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "M", M) &&
             read_int(p, end, "kmax", kmax) && read_int(p, end, "precision", prec) &&
             read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
             read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
@@ -86,6 +138,16 @@ void save_locked() {
     if (!f) return;
     fprintf(f, "[\n");
     size_t i = 0;
+    const size_t count = g_table.size() + g_btable.size();
+    for (const auto &kv : g_btable) {
+        const BKey &k = kv.first;
+        const BEntry &e = kv.second;
+        fprintf(f,
+                "  {\"cc\": %d, \"sms\": %d, \"precision\": %d, \"batch\": \"%016llx\", \"n\": %d, \"grain\": %d, "
+                "\"ccap\": %d, \"variant\": %d, \"ms\": %.4f}%s\n",
+                std::get<0>(k), std::get<1>(k), std::get<2>(k), (unsigned long long)std::get<3>(k), e.n, e.cfg.grain,
+                e.cfg.ccap, e.cfg.variant, e.ms, ++i < count ? "," : "");
+    }
     for (const auto &kv : g_table) {
         const Key &k = kv.first;
         const Entry &e = kv.second;
@@ -93,7 +155,7 @@ void save_locked() {
                 "  {\"cc\": %d, \"sms\": %d, \"M\": %d, \"kmax\": %d, \"precision\": %d, \"grain\": %d, "
                 "\"ccap\": %d, \"variant\": %d, \"ms\": %.4f}%s\n",
                 std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), e.cfg.grain,
-                e.cfg.ccap, e.cfg.variant, e.ms, ++i < g_table.size() ? "," : "");
+                e.cfg.ccap, e.cfg.variant, e.ms, ++i < count ? "," : "");
     }
     fprintf(f, "]\n");
     fclose(f);
@@ -115,6 +177,24 @@ TreeCfg tuned_cfg(int sms, int M, int kmax, int precision) {
     load_locked();
     auto it = g_table.find(Key{device_cc(), sms, M, kmax, precision});
     return it == g_table.end() ? kDefaultCfg : it->second.cfg;
+}
+
+bool tuned_batch_cfg(int sms, const gbs_instance *inst, int n, int precision, TreeCfg &cfg) {
+    const uint64_t sig = batch_signature(inst, n);
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_locked();
+    auto it = g_btable.find(BKey{device_cc(), sms, precision, sig});
+    if (it == g_btable.end()) return false;
+    cfg = it->second.cfg;
+    return true;
+}
+
+void record_batch_cfg(int sms, const gbs_instance *inst, int n, int precision, const TreeCfg &cfg, float ms) {
+    const uint64_t sig = batch_signature(inst, n);
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_locked();
+    g_btable[BKey{device_cc(), sms, precision, sig}] = BEntry{cfg, ms, n};
+    save_locked();
 }
 
 int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tried) {
