@@ -6,11 +6,19 @@ r~U[0.8,1.6], Haar U(144), eta_i~U[0.3,0.5]), inputs already in HBM. value =
 subsets/s over the timed steps (device time, CUDA events on the call's stream).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32r|fp64]
-                  [--impl ours|reference]
+                  [--impl ours|reference] [--workload ...]
 
 The headline is the refined-FP32 path (FP32 determinant steps refined to FP64
 accuracy, FP64 sums); the plain FP64 path is timed in the same run and reported
-under "fp64_path".
+under "fp64_path". The default run also measures, with fewer steps, the other
+workloads (each also runnable alone with --workload) and attaches them under
+"workloads": the 256-instance ragged batch, the M=100 fitting step (forward and
+adjoint), the displaced-state table and the K=5 sampler.
+
+Rooflines: the FP64 and FP32 pipe peaks are measured in the same run by the
+library's probe (gbs_pipe_peaks); the HBM peak is the measured copy bandwidth of
+the machine; per-entry instruction counts and DRAM traffic come from ncu
+captures of the same kernels (OPS_PER_ENTRY, TRAFFIC_BYTES below).
 
 --impl reference times the CPU oracle (plain FP64 loops, LU determinants and
 explicit partitions) on the host cores, each step a bounded random sample of the
@@ -27,6 +35,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from math import comb
 
 import numpy as np
 
@@ -36,18 +45,27 @@ sys.path.insert(0, ROOT)
 METRIC = "subsets/s and wall time for the order-≤5 M=144 cumulant table, mixed vs FP64 GPU"
 WORKLOAD = ("M=144 kmax=5 click-cumulant table: 72 squeezers r~U[0.8,1.6] on modes 0-71, Haar U(144), "
             "eta_i~U[0.3,0.5], seed 20251116")
-# FP64 flops per order-5 entry of the cumulant table (FMA = 2). FP64 path: 2x2
-# cross update 16, triangular solve 8, Schur step 12, determinant 3,
-# P0 = P0(S') det^{-1/2} 3, cumulant recursion 15 FMA = 30. Refined path: the
-# determinant step runs on the FP32 pipe; FP64 keeps the P0 product (3) and the
-# recursion (30).
-FP64_FLOPS_PER_LEAF = {"fp64": 72, "fp32r": 33}
 DTYPE = {"fp64": "f64", "fp32r": "f32 determinant steps refined to f64 accuracy; f64 sums"}
-# DRAM bytes (read + write) per launch of the order-5 kernel at M=144 under the
-# tuned schedules, from the ncu launch list in profiles/launches_m144k5_tuned.md.
-# Reset to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES = {"fp32r": 6.2201e9 + 4.2769e9, "fp64": 3.1267e9 + 4.2348e9}
-FP64_FMA_PER_CLK_PER_SM = 2  # nominal 1.25 TFLOP/s over 152 SMs at 2.07 GHz
+
+# Executed thread instructions per table entry of each prefix-tree kernel (ncu
+# SASS counters sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,fp32}_pred_on
+# divided by the launch's entries, one capture of the M=144 kmax=5 cumulant call
+# under the tuned schedules). They include the amortised per-item
+# Schur-complement build and per-child eliminations. None = not captured for the
+# kernel as it stands.
+OPS_PER_ENTRY = {
+    ("fp32r", 5): {"dfma": 15.021, "dadd": 0.014, "dmul": 1.019, "fp32": 416.13},
+    ("fp32r", 4): {"dfma": 8.009, "dadd": 0.013, "dmul": 1.014, "fp32": 410.63},
+    ("fp64", 5): {"dfma": 36.138, "dadd": 0.001, "dmul": 8.406, "fp32": 4.058},
+    ("fp64", 4): {"dfma": 28.533, "dadd": 0.002, "dmul": 8.324, "fp32": 5.308},
+}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# order-5 kernel at M=144 under the tuned schedule (ncu, that kernel alone, one
+# launch); None once the kernel has changed since the capture.
+TRAFFIC_BYTES = {"fp32r": None, "fp64": None}
+NOMINAL_FP64_FMA_PER_CLK_PER_SM = 2
+NOMINAL_FP32_FMA_PER_CLK_PER_SM = 128
+HBM_FALLBACK_GBS = 6800.0
 
 
 def parse():
@@ -63,6 +81,8 @@ def parse():
                    help="skip gbs_autotune (untimed) before measuring; use the default schedule")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-workloads", action="store_true",
+                   help="default run: skip the secondary workloads (batch, fitting, displaced, sampler)")
     p.add_argument("--batch", type=int, default=8192, help="samples per step (sample144)")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
     p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "disp144", "sample144"],
@@ -96,10 +116,84 @@ def replica_value(n_entries, steps, world, total_ms):
     return n_entries * steps * world / (total_ms * 1e-3)
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------- rooflines
+
+def tree_bytes(M, d, kmax):
+    """Algorithmic DRAM bytes of the order-d kernel: its entries written once
+    (the output table, and the P0 table too below the top order) and every
+    lower-order entry of both tables read once."""
+    n = comb(M, d)
+    written = 8 * n * (2 if d < kmax else 1)
+    read = 2 * 8 * sum(comb(M, e) for e in range(1, d))
+    return written + read
+
+
+def pipe_fracs(ops, n_entries, ms, peaks, sms, sm_mhz):
+    """FP64 and FP32 pipe rooflines of n_entries entries in ms, given executed
+    instructions per entry (an FMA counts 2 flops)."""
+    t = ms * 1e-3
+    f64 = (2 * ops["dfma"] + ops["dadd"] + ops["dmul"]) * n_entries / t
+    i64 = (ops["dfma"] + ops["dadd"] + ops["dmul"]) * n_entries / t
+    f32i = ops["fp32"] * n_entries / t
+    nominal64 = 2 * NOMINAL_FP64_FMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6
+    nominal32 = 2 * NOMINAL_FP32_FMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6
+    return {
+        "fp64": {"achieved_tflops": f64 / 1e12, "peak_tflops": peaks["fp64_flops"] / 1e12,
+                 "frac": f64 / peaks["fp64_flops"], "frac_of_nominal": f64 / nominal64,
+                 "pipe_instr_per_entry": ops["dfma"] + ops["dadd"] + ops["dmul"],
+                 "pipe_frac": i64 / (peaks["fp64_flops"] / 2)},
+        "fp32": {"instr_per_entry": ops["fp32"], "pipe_frac": f32i / (peaks["fp32_flops"] / 2),
+                 "pipe_frac_of_nominal": f32i / (nominal32 / 2)},
+    }
+
+
+def tree_roofline(prec, M, d, kmax, ms, peaks, sms, sm_mhz, hbm):
+    n = comb(M, d)
+    alg = tree_bytes(M, d, kmax)
+    out = {"kernel": f"tree_kernel<{d}, kappa, {prec}>", "entries": n, "ms": ms,
+           "dram": {"algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm[0],
+                    "frac": alg / (ms * 1e-3) / 1e9 / hbm[0]}}
+    ops = OPS_PER_ENTRY.get((prec, d))
+    if ops:
+        out.update(pipe_fracs(ops, n, ms, peaks, sms, sm_mhz))
+    if d == 5 and M == 144 and TRAFFIC_BYTES.get(prec):
+        out["dram"]["traffic"] = TRAFFIC_BYTES[prec]
+        out["dram"]["traffic_over_algorithmic"] = TRAFFIC_BYTES[prec] / alg
+    return out
+
+
+def headline_roofline(prec, M, kmax, order_ms, peaks, sms, sm_mhz, hbm):
+    """The dominant kernel (order kmax) in the contract's form, its pipes, and every
+    prefix-tree kernel of the call."""
+    kernels = [tree_roofline(prec, M, d, kmax, order_ms[d], peaks, sms, sm_mhz, hbm)
+               for d in range(4, kmax + 1) if order_ms[d] > 0]
+    top = kernels[-1]
+    fp64 = top.get("fp64")
+    return {"bound": "alu", "kernel": f"{top['kernel']} (FP64 pipe)",
+            "achieved": fp64["achieved_tflops"] if fp64 else None,
+            "peak": peaks["fp64_flops"] / 1e12, "unit": "TFLOP/s",
+            "frac": fp64["frac"] if fp64 else None,
+            "traffic": TRAFFIC_BYTES.get(prec) if M == 144 else None,
+            "peak_source": "measured in this run by gbs_pipe_peaks (sustained FP64 FMA throughput), of measured",
+            "kernel_ms": order_ms[kmax], "order_ms": list(order_ms),
+            "pipes": {k: top[k] for k in ("fp64", "fp32", "dram") if k in top},
+            "kernels": kernels}
+
+
+# ---------------------------------------------------------------- CPU oracle
+
 def sample_subsets(M, kmax, n, seed):
     """n subsets of the workload with the table's order mix (order d with
     probability C(M,d)/N), as (d, rows) groups."""
-    from math import comb
     import synthetic
     rng = np.random.default_rng(seed)
     sizes = np.array([comb(M, d) for d in range(1, kmax + 1)], dtype=float)
@@ -131,7 +225,7 @@ def cpu_baseline(inst, target_s=12.0, n=0):
 class ClockSampler:
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(tempfile.gettempdir(), f"gbs_bench_clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gbs_bench_clocks_{os.getpid()}_{id(self)}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -207,6 +301,8 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- headline
+
 def measure(gbs, torch, V, out, ws, kmax, prec, steps, warmup, flush, stream, dev):
     """K timed steps of one precision: per-step CUDA events (L2 flushed between
     steps, outside the events) and per-order kernel times from the library."""
@@ -237,80 +333,92 @@ def measure(gbs, torch, V, out, ws, kmax, prec, steps, warmup, flush, stream, de
     return float(sum(step_ms)), order_ms / steps, wall
 
 
-def roofline(prec, M, order_ms, sms, sm_max_mhz):
-    from math import comb
-    t5 = order_ms[5]
-    traffic = TRAFFIC_BYTES.get(prec) if M == 144 else None
-    peak = FP64_FMA_PER_CLK_PER_SM * 2 * sms * sm_max_mhz * 1e6
-    achieved = FP64_FLOPS_PER_LEAF[prec] * comb(M, 5) / (t5 * 1e-3)
-    return {"bound": "alu", "kernel": f"tree_kernel<5, kappa, {prec}> (FP64 pipe)", "achieved": achieved / 1e12,
-            "peak": peak / 1e12, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                              "profiles/launches_m144k5_tuned.md" if traffic else None,
-            "peak_source": "derived: 2 FP64 FMA/clk/SM x SMs x max SM clock (nominal 1.25 TFLOP/s at 2.07 GHz)",
-            "flops_per_entry": FP64_FLOPS_PER_LEAF[prec], "kernel_ms": t5, "order_ms": order_ms.tolist()}
+# ---------------------------------------------------------------- secondary workloads
 
-
-def bench_batch(args):
-    """256 ragged instances: one batched launch (CUDA-graph replay) in the headline
+def run_batch(precision, steps, warmup, autotune, peaks, sms, sm_mhz):
+    """256 ragged instances: one batched launch (CUDA-graph replay) in the given
     precision vs one gbs_cumulants call per instance in FP64."""
     import torch
     import synthetic
     import paper_2511_14923_gb300 as gbs
-    gbs.build()
     insts = synthetic.batch_instances(256)
     N = sum(gbs.table_size(x.M, x.kmax) for x in insts)
     Vs = [torch.from_numpy(x.V).cuda() for x in insts]
     # untimed: the batch autotuner picks the batched kernel's schedule for this batch
-    b = gbs.Batch(Vs, [x.kmax for x in insts], args.precision, autotune=not args.no_autotune)
+    b = gbs.Batch(Vs, [x.kmax for x in insts], precision, autotune=autotune)
     b.capture()
-    for _ in range(max(args.warmup - 1, 0)):
+    for _ in range(max(warmup - 1, 0)):
         b.replay()
     if b.status() != 0:
         raise SystemExit("batched launch reported a device error")
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        b.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / args.steps
+    with ClockSampler() as clk:
+        for a, e in ev:
+            a.record()
+            b.replay()
+            e.record()
+        torch.cuda.synchronize()
+    ms_batch = sum(a.elapsed_time(e) for a, e in ev) / steps
     # per-instance FP64 launches into the same outputs
     wss = {}
     for x in insts:
         key = (x.M, x.kmax)
         if key not in wss:
             wss[key] = gbs.Workspace(x.M, x.kmax, "fp64")
+
     def per_instance(prec):
         for V, x, o in zip(Vs, insts, b.outputs):
             gbs.cumulants(V, x.kmax, prec, out=o, workspace=wss[(x.M, x.kmax)], check=False)
     per_instance("fp64")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    n_single = max(1, steps // 2)
     e0.record()
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(n_single):
         per_instance("fp64")
     e1.record()
     torch.cuda.synchronize()
-    ms_single = e0.elapsed_time(e1) / max(1, args.steps // 2)
-    line = {"metric": "subsets/s of the 256-instance ragged batch (click-cumulant tables)", "value": N / (ms_batch * 1e-3),
-            "unit": "subsets/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
-            "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": "256 instances, M~U{16..144}, kmax~U{2..5}, r~U[0.5,1.5] on the first M/2 modes, "
-                                   "eta_i~U[0.2,0.6], seed 20251118", "subsets": N, "table_bytes": N * 8,
-                       "launch": "one persistent cooperative kernel, CUDA-graph replay", "precision": args.precision},
-            "schedule": b.schedule(), "autotune_best_ms": b.tune_ms,
-            "per_instance_fp64": {"ms_per_step": ms_single, "value": N / (ms_single * 1e-3), "launches": 6 * len(insts)}}
-    print(json.dumps(line), flush=True)
+    ms_single = e0.elapsed_time(e1) / n_single
+    # roofline of the one batched kernel: its order-4 and order-5 leaves at the
+    # per-entry counts of the single-instance kernels (same device code); orders
+    # 1-3 and packing are under 0.1 % of the entries
+    ent = {d: sum(comb(x.M, d) for x in insts if x.kmax >= d) for d in (4, 5)}
+    roof = {"kernel": f"batched_kernel<{precision}, {b.schedule()['cta_shape']}>", "ms": ms_batch,
+            "entries_order4": ent[4], "entries_order5": ent[5]}
+    o4, o5 = OPS_PER_ENTRY.get((precision, 4)), OPS_PER_ENTRY.get((precision, 5))
+    if o4 and o5:
+        mix = {k: (o4[k] * ent[4] + o5[k] * ent[5]) / (ent[4] + ent[5]) for k in o5}
+        roof.update(pipe_fracs(mix, ent[4] + ent[5], ms_batch, peaks, sms, sm_mhz))
+    rec = {"metric": "subsets/s of the 256-instance ragged batch (click-cumulant tables)",
+           "value": N / (ms_batch * 1e-3), "unit": "subsets/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms_batch, "higher_is_better": True, "dtype": DTYPE[precision], "data": "synthetic",
+           "config": {"workload": "256 instances, M~U{16..144}, kmax~U{2..5}, r~U[0.5,1.5] on the first M/2 modes, "
+                                  "eta_i~U[0.2,0.6], seed 20251118", "subsets": N, "table_bytes": N * 8,
+                      "launch": "one persistent cooperative kernel, CUDA-graph replay", "precision": precision,
+                      "l2": "43 GB of outputs per step, far above L2"},
+           "schedule": b.schedule(), "autotune_best_ms": b.tune_ms, "gpu_launches": steps,
+           "per_instance_fp64": {"ms_per_step": ms_single, "value": N / (ms_single * 1e-3),
+                                 "launches": 6 * len(insts)},
+           "roofline": roof, "clocks": clk.summary()}
+    del b, Vs
+    torch.cuda.empty_cache()
+    return rec
 
 
-def bench_fit(args):
+# FP64 flops (FMA = 2) of the adjoint phases at M=100, kmax=4, from the ncu SASS
+# counters of one gbs_cumulants_backward call (sum over the phase's kernels);
+# None = not captured.
+FIT_PHASE_FP64_FLOPS = {"p0_recompute": 235197625, "h_table": 2293700, "gp0_gather": 194452675,
+                        "gv_scatter": 2029657521}
+
+
+def run_fit(steps, warmup, peaks):
     """Fitting step on the M=100, kmax=4 workload: r, eta -> V -> kt -> weighted
     squared error against a target table, then the adjoint back to r and eta."""
     import torch
     import synthetic
     import paper_2511_14923_gb300 as gbs
-    gbs.build()
     inst = synthetic.config(3)
     tgt = synthetic.fit_target(inst)
     M, K = inst.M, inst.kmax
@@ -326,32 +434,55 @@ def bench_fit(args):
         L = (w * (kt - kt_t) ** 2).sum()
         return torch.autograd.grad(L, (r, eta))
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    with ClockSampler() as clk:
+        for a, e in ev:
+            a.record()
+            step()
+            e.record()
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    # the adjoint's phases (one more call with the library's events on)
+    V = gbs.covariance(U, r.detach(), eta.detach())
+    g = torch.randn(gbs.table_size(M, K), dtype=torch.float64, device="cuda")
+    gbs.cumulants_backward(V, K, g)
+    gbs.timing(True)
+    phases = np.zeros(4)
+    for _ in range(3):
+        gbs.cumulants_backward(V, K, g, check=False)
+        phases += np.array(gbs.timing_read_backward())
+    gbs.timing(False)
+    phases /= 3
+    names = ["p0_recompute", "h_table", "gp0_gather", "gv_scatter"]
+    roof = {"phases_ms": dict(zip(names, phases.tolist()))}
+    if FIT_PHASE_FP64_FLOPS:
+        roof["fp64"] = {k: {"achieved_tflops": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / 1e12,
+                            "frac": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / peaks["fp64_flops"]}
+                        for k, t in zip(names, phases) if k in FIT_PHASE_FP64_FLOPS and t > 0}
     N = gbs.table_size(M, K)
-    print(json.dumps({"metric": "fitting step (forward + adjoint), M=100 kmax=4", "value": N / (ms * 1e-3),
-                      "unit": "subsets/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "M=100 kmax=4, 50 squeezers, per-mode eta; target from seed + 1",
-                                 "subsets": N, "params": 2 * M}}), flush=True)
+    return {"metric": "fitting step (forward + adjoint), M=100 kmax=4", "value": N / (ms * 1e-3),
+            "unit": "subsets/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "M=100 kmax=4, 50 squeezers, per-mode eta; target from seed + 1",
+                       "subsets": N, "params": 2 * M},
+            "roofline": roof, "clocks": clk.summary()}
 
 
-def bench_displaced(args):
+# FP64 pipe instructions (DFMA + DADD + DMUL) and FP32 instructions per entry of
+# the displaced-state order-5 kernel at M=144 (ncu SASS counters); None = not captured.
+DISP_OPS_PER_ENTRY = {"dfma": 56.324, "dadd": 1.001, "dmul": 16.480, "fp32": 5.058}
+
+
+def run_displaced(steps, warmup, peaks, sms, sm_mhz):
     """Displaced-state click-cumulant table, M=144 kmax=5 (the headline instance fed
     with coherent input displacements, |alpha| ~ 0.5), FP64, beside the zero-mean
     FP64 table of the same covariance."""
     import torch
     import synthetic
     import paper_2511_14923_gb300 as gbs
-    gbs.build()
     inst = synthetic.config(2)
     mean = synthetic.displaced_mean(inst, seed=2025, alpha_scale=0.5)
     V = torch.from_numpy(inst.V).cuda()
@@ -361,42 +492,50 @@ def bench_displaced(args):
     ws = gbs.Workspace(inst.M, inst.kmax, "fp64")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     res = {}
-    for name, fn in (("displaced", lambda: gbs.displaced_tables(V, m, 5, "kappa", out=out, workspace=ws, check=False)),
-                     ("zero_mean", lambda: gbs.cumulants(V, 5, "fp64", out=out, workspace=ws, check=False))):
-        for _ in range(args.warmup):
-            fn()
-        if ws.status() != 0:
-            raise SystemExit(f"{name}: device status {ws.status()}")
-        gbs.timing(True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        order_ms = np.zeros(6)
-        for s, (a, b) in enumerate(ev):
-            flush.fill_(float(s))
-            a.record()
-            fn()
-            b.record()
-            order_ms += np.array(gbs.timing_read())
-        torch.cuda.synchronize()
-        gbs.timing(False)
-        res[name] = (sum(a.elapsed_time(b) for a, b in ev) / args.steps, (order_ms / args.steps).tolist())
+    with ClockSampler() as clk:
+        for name, fn in (("displaced", lambda: gbs.displaced_tables(V, m, 5, "kappa", out=out, workspace=ws,
+                                                                    check=False)),
+                         ("zero_mean", lambda: gbs.cumulants(V, 5, "fp64", out=out, workspace=ws, check=False))):
+            for _ in range(warmup):
+                fn()
+            if ws.status() != 0:
+                raise SystemExit(f"{name}: device status {ws.status()}")
+            gbs.timing(True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            order_ms = np.zeros(6)
+            for s, (a, b) in enumerate(ev):
+                flush.fill_(float(s))
+                a.record()
+                fn()
+                b.record()
+                order_ms += np.array(gbs.timing_read())
+            torch.cuda.synchronize()
+            gbs.timing(False)
+            res[name] = (sum(a.elapsed_time(b) for a, b in ev) / steps, (order_ms / steps).tolist())
     ms = res["displaced"][0]
-    print(json.dumps({"metric": "subsets/s, displaced-state click-cumulant table M=144 kmax=5",
-                      "value": N / (ms * 1e-3), "unit": "subsets/s", "ms_per_step": ms, "steps": args.steps,
-                      "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "M=144 kmax=5 instance with coherent input displacements "
-                                             "(alpha ~ 0.5 (N + iN)/sqrt 2, seed 2025)", "subsets": N,
-                                 "l2": "flushed between steps"},
-                      "order_ms": res["displaced"][1],
-                      "zero_mean_fp64": {"ms_per_step": res["zero_mean"][0], "order_ms": res["zero_mean"][1]}}),
-          flush=True)
+    t5 = res["displaced"][1][5]
+    roof = {"kernel": "tree_kernel<5, kappa, fp64, displaced>", "ms": t5}
+    if DISP_OPS_PER_ENTRY:
+        roof.update(pipe_fracs(DISP_OPS_PER_ENTRY, comb(inst.M, 5), t5, peaks, sms, sm_mhz))
+    rec = {"metric": "subsets/s, displaced-state click-cumulant table M=144 kmax=5",
+           "value": N / (ms * 1e-3), "unit": "subsets/s", "ms_per_step": ms, "steps": steps,
+           "warmup": warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "M=144 kmax=5 instance with coherent input displacements "
+                                  "(alpha ~ 0.5 (N + iN)/sqrt 2, seed 2025)", "subsets": N,
+                      "l2": "flushed between steps"},
+           "order_ms": res["displaced"][1], "roofline": roof, "clocks": clk.summary(),
+           "zero_mean_fp64": {"ms_per_step": res["zero_mean"][0], "order_ms": res["zero_mean"][1]}}
+    del out, ws, flush
+    torch.cuda.empty_cache()
+    return rec
 
 
 PAPER_SAMPLES_PER_GPU_S = 1e7 / (115 * 60) / 8  # 10^7 samples in 115 min on 8 H100 (K = 5, M = 144)
 
 
-def bench_sampler(args):
+def run_sampler(args, steps, warmup, batch, hbm, with_fp64=True, with_e2e=True):
     """Stage 2: K = 5 double-elision samples of the M=144 workload's spin-cumulant
-    table (FP32 tables, as the paper stores them), one gbs_sample call of --batch
+    table (FP32 tables, as the paper stores them), one gbs_sample call of batch
     samples per step; uniforms seeded and resident on the device. The FP64 form is
     timed beside it on a smaller batch. Under torchrun every rank draws its own
     samples (rank-seeded uniforms, no exchange): weak scaling, the slowest rank's
@@ -404,15 +543,16 @@ def bench_sampler(args):
     import torch
     import synthetic
     import paper_2511_14923_gb300 as gbs
-    rank, world, dist = dist_init(args.gpus)
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    gbs.build()
-    M, K, B = 144, 5, args.batch
+    M, K, B = 144, 5, batch
     inst = synthetic.config(2)
     kap = gbs.spin_cumulants(torch.from_numpy(inst.V).cuda(), K, "fp64")
     g = torch.Generator(device="cuda").manual_seed(20251114 + 1000 * rank)
-    steps, warm = args.steps, max(args.warmup, 3)
+    warm = max(warmup, 3)
     us = [torch.rand(B, M, dtype=torch.float64, device="cuda", generator=g) for _ in range(steps + warm)]
     ws = torch.empty(gbs.sampler_workspace_bytes(M, K, B, "fp32"), dtype=torch.uint8, device="cuda")
     for w in range(warm):
@@ -432,47 +572,86 @@ def bench_sampler(args):
         dist.barrier()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dist, torch.device("cuda", local))
     ok = bool(torch.isfinite(logp).all())
-    # end to end: uniforms from pinned host memory in, bitstrings out, every step
-    uh = us[0].cpu().pin_memory()
-    bh = torch.empty((B, M), dtype=torch.uint8).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ud = torch.empty_like(us[0])
-    e0.record()
-    for _ in range(steps):
-        ud.copy_(uh, non_blocking=True)
-        bits, _, _ = gbs.sample(kap, M, K, u=ud, batch=B, precision="fp32", workspace=ws, check=False)
-        bh.copy_(bits, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps, dist, torch.device("cuda", local))
-    # FP64 tables on a smaller batch
-    B64 = 512
-    ws64 = torch.empty(gbs.sampler_workspace_bytes(M, K, B64, "fp64"), dtype=torch.uint8, device="cuda")
-    gbs.sample(kap, M, K, u=us[0][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64)
-    e0.record()
-    gbs.sample(kap, M, K, u=us[1][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64, check=False)
-    e1.record()
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1)
-    value = B * world / (ms * 1e-3)
-    if rank != 0:
-        return
-    print(json.dumps({
-        "metric": "samples/s, K=5 double-elision chain-rule sampler, M=144", "value": value, "unit": "samples/s",
-        "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "spin cumulants of the M=144 kmax=5 workload (72 squeezers, per-mode eta), "
-                               "K=5 double elision, orders (3, 3, 2), FP32 tables", "samples_per_step_per_gpu": B,
-                   "parallelism": f"{world} independent sampler(s), rank-seeded uniforms, no exchange",
-                   "inputs": f"{B} x {M} seeded uniforms per step, resident on the device",
-                   "workspace_GB": ws.numel() / 1e9, "l2": "per-step working set (tables of 8192 samples) >> L2"},
-        "paper_context": {"samples_per_s_per_gpu": PAPER_SAMPLES_PER_GPU_S,
-                          "hardware": "8x H100 SXM, 1e7 samples in 115 min",
-                          "ratio_per_gpu": value / world / PAPER_SAMPLES_PER_GPU_S},
-        "fp64_tables": {"samples_per_step": B64, "ms_per_step": ms64, "value": B64 / (ms64 * 1e-3)},
-        "e2e": {"value": B * world / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": B * M * 8,
-                "d2h_bytes_per_step": B * M},
-        "all_finite": ok, "clocks": clk.summary()}), flush=True)
+    rec = {"metric": "samples/s, K=5 double-elision chain-rule sampler, M=144", "value": B * world / (ms * 1e-3),
+           "unit": "samples/s", "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "spin cumulants of the M=144 kmax=5 workload (72 squeezers, per-mode eta), "
+                                  "K=5 double elision, orders (3, 3, 2), FP32 tables",
+                      "samples_per_step_per_gpu": B,
+                      "parallelism": f"{world} independent sampler(s), rank-seeded uniforms, no exchange",
+                      "inputs": f"{B} x {M} seeded uniforms per step, resident on the device",
+                      "workspace_GB": ws.numel() / 1e9, "l2": "per-step working set (tables of 8192 samples) >> L2"},
+           "paper_context": {"samples_per_s_per_gpu": PAPER_SAMPLES_PER_GPU_S,
+                             "hardware": "8x H100 SXM, 1e7 samples in 115 min",
+                             "ratio_per_gpu": B / (ms * 1e-3) / PAPER_SAMPLES_PER_GPU_S},
+           # the p2 table's reads (rows below n of every sample's table at each step
+           # n: 4 B x C(M, 4) per sample) over the whole call: a lower bound on the
+           # bandwidth the call achieves
+           "roofline": {"bound": "hbm", "p2_bytes_per_call": 4 * comb(M, 4) * B,
+                        "achieved_gbs_call_average": 4 * comb(M, 4) * B / (ms * 1e-3) / 1e9,
+                        "peak_gbs": hbm[0],
+                        "frac_call_average": 4 * comb(M, 4) * B / (ms * 1e-3) / 1e9 / hbm[0]},
+           "all_finite": ok, "clocks": clk.summary()}
+    if with_e2e:
+        # end to end: uniforms from pinned host memory in, bitstrings out, every step
+        uh = us[0].cpu().pin_memory()
+        bh = torch.empty((B, M), dtype=torch.uint8).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ud = torch.empty_like(us[0])
+        e0.record()
+        for _ in range(steps):
+            ud.copy_(uh, non_blocking=True)
+            bits, _, _ = gbs.sample(kap, M, K, u=ud, batch=B, precision="fp32", workspace=ws, check=False)
+            bh.copy_(bits, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps, dist, torch.device("cuda", local))
+        rec["e2e"] = {"value": B * world / (ms_e2e * 1e-3), "unit": "samples/s", "h2d_bytes_per_step": B * M * 8,
+                      "d2h_bytes_per_step": B * M}
+    del ws
+    torch.cuda.empty_cache()
+    if with_fp64:
+        B64 = 512
+        ws64 = torch.empty(gbs.sampler_workspace_bytes(M, K, B64, "fp64"), dtype=torch.uint8, device="cuda")
+        gbs.sample(kap, M, K, u=us[0][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gbs.sample(kap, M, K, u=us[1][:B64].contiguous(), batch=B64, precision="fp64", workspace=ws64, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        rec["fp64_tables"] = {"samples_per_step": B64, "ms_per_step": ms64, "value": B64 / (ms64 * 1e-3)}
+        del ws64
+    del us
+    torch.cuda.empty_cache()
+    return rec
+
+
+def standalone(args, which):
+    """--workload batch256 | fit100 | disp144 | sample144: that workload alone."""
+    import torch
+    import paper_2511_14923_gb300 as gbs
+    if which == "sample144":
+        dist_init(args.gpus)
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    gbs.build()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = gbs.pipe_peaks()
+    hbm = hbm_peak_gbs()
+    mhz = peaks["sm_mhz_fp64_probe"]
+    if which == "batch256":
+        rec = run_batch(args.precision, args.steps, args.warmup, not args.no_autotune, peaks, sms, mhz)
+    elif which == "fit100":
+        rec = run_fit(args.steps, args.warmup, peaks)
+    elif which == "disp144":
+        rec = run_displaced(args.steps, args.warmup, peaks, sms, mhz)
+    else:
+        rec = run_sampler(args, args.steps, args.warmup, args.batch, hbm)
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+    rec["pipe_peaks_measured"] = peaks
+    print(json.dumps(rec), flush=True)
 
 
 def main():
@@ -480,17 +659,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "batch256":
-        bench_batch(args)
-        return
-    if args.workload == "sample144":
-        bench_sampler(args)
-        return
-    if args.workload == "disp144":
-        bench_displaced(args)
-        return
-    if args.workload == "fit100":
-        bench_fit(args)
+    if args.workload in ("batch256", "sample144", "disp144", "fit100"):
+        standalone(args, args.workload)
         return
     import torch
     import synthetic
@@ -517,6 +687,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream(dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = gbs.pipe_peaks(dev)  # untimed: the FP64 / FP32 pipe peaks of this GPU
+    hbm = hbm_peak_gbs()
 
     tuned = {}
     if not args.no_autotune:
@@ -530,7 +702,7 @@ def main():
         for p in precs:
             res[p] = measure(gbs, torch, V, out, wss[p], kmax, p, args.steps, args.warmup, flush, stream, dev)
     clocks = clk.summary(local)
-    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    sm_mhz = clocks.get("sm_mhz") or peaks["sm_mhz_fp64_probe"]
 
     tot = {p: max_over_ranks(res[p][0], dist, dev) for p in precs}
     value = replica_value(N, args.steps, world, tot[head])
@@ -587,6 +759,19 @@ def main():
                "h2d_bytes_per_step": int(hV.numel() * 8), "d2h_bytes_per_step": int(N * 8),
                "pipelined": "table of step k copied back while step k+1 computes (two device buffers)",
                "sequential_ms_per_step": seq_ms, "sequential_value": N * world / (seq_ms * 1e-3)}
+        del hout, outs, dV
+    del out, wss, flush
+    torch.cuda.empty_cache()
+
+    workloads = None
+    if not args.no_workloads and args.workload == "m144k5" and world == 1:
+        w_steps, w_warm = 3, 3
+        workloads = {
+            "batch256": run_batch(head, w_steps, w_warm, not args.no_autotune, peaks, sms, sm_mhz),
+            "fit100": run_fit(5, w_warm, peaks),
+            "disp144": run_displaced(w_steps, w_warm, peaks, sms, sm_mhz),
+            "sample144": run_sampler(args, w_steps, w_warm, args.batch, hbm, with_fp64=False, with_e2e=False),
+        }
 
     if rank == 0:
         cpu = None
@@ -601,12 +786,16 @@ def main():
                                  "the 3.99 GB output also exceeds L2",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "autotune_best_ms": tuned or None,
-                "wall_s_timed": res[head][2], "roofline": roofline(head, M, res[head][1], sms, sm_max),
+                "wall_s_timed": res[head][2],
+                "roofline": headline_roofline(head, M, kmax, res[head][1], peaks, sms, sm_mhz, hbm),
+                "pipe_peaks_measured": peaks, "hbm_peak": {"gbs": hbm[0], "source": hbm[1]},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 6 * args.steps, "clocks": clocks}
         for p in precs[1:]:
             line[f"{p}_path"] = {"value": replica_value(N, args.steps, world, tot[p]), "unit": "subsets/s",
                                  "ms_per_step": tot[p] / args.steps, "dtype": DTYPE[p],
-                                 "roofline": roofline(p, M, res[p][1], sms, sm_max)}
+                                 "roofline": headline_roofline(p, M, kmax, res[p][1], peaks, sms, sm_mhz, hbm)}
+        if workloads:
+            line["workloads"] = workloads
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -133,6 +133,30 @@ int gbs_spin_cumulants(const double *V, int M, int kmax, double *kappa_out, int 
 int gbs_timing(int on);
 int gbs_timing_read(float *ms_out);
 
+/* The same for gbs_cumulants_backward: while timing is enabled, its phases are
+   bracketed by events, and this waits for those of the most recent backward call
+   and writes ms_out[0] = recomputation of the P0 table (forward kernels),
+   ms_out[1] = the inverse-moment table h, ms_out[2] = the dL/dP0 gather,
+   ms_out[3] = the dL/dV scatter (block inverses, per-prefix accumulation,
+   mirroring). Returns GBS_OK, GBS_ERR_INVALID_ARG (no timed backward call) or
+   GBS_ERR_CUDA. */
+int gbs_timing_read_backward(float *ms_out);
+
+/* Bytes of device scratch gbs_pipe_peaks needs. */
+#define GBS_PIPE_PEAKS_SCRATCH 65536
+
+/* Sustained multiply-add throughput of the current GPU's FP64 and FP32 pipes,
+   the peaks against which the kernels' arithmetic rooflines are reported (not
+   part of the paper's method). Runs two probe kernels of about 40 ms each on
+   cuda_stream -- every thread keeps 8 independent FMA chains busy, 32 warps per
+   multiprocessor -- and synchronises it. scratch: device memory of at least
+   GBS_PIPE_PEAKS_SCRATCH bytes (overwritten). out (host, 6 doubles): FP64
+   FLOP/s, FP32 FLOP/s (an FMA counts 2), FP64 and FP32 FMAs per clock per
+   multiprocessor, and the median SM clock in MHz seen by the FP64 and the FP32
+   probe (from each block's cycle counter against the global nanosecond timer).
+   Returns GBS_OK, GBS_ERR_INVALID_ARG or GBS_ERR_CUDA. */
+int gbs_pipe_peaks(double *out, void *scratch, void *cuda_stream);
+
 /* ---------------------------------------------------------------- forward tables */
 
 /* P0 table: p0_out[gbs_table_size(M,kmax)] <- P0(S) for every 1 <= |S| <= kmax
@@ -223,8 +247,9 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
 /* Times gbs_cumulants for this (M, kmax, precision) under each candidate
    schedule of the prefix-tree kernels -- items per CTA (1, 2, 4, 8), children
    per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, 256 x 2
-   per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, and 256 x 3 when
-   M <= 577) -- and records the fastest in a process-wide table that
+   per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, 256 x 3 when
+   M <= 577, and 768 x 1 with a larger shared-memory batch area) -- and records
+   the fastest in a process-wide table that
    later forward calls of that shape use. If the environment variable
    GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and
    rewritten after tuning (JSON). Arguments as for gbs_cumulants; kappa_out is
@@ -280,7 +305,7 @@ int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream);
 /* Batch autotuner (the schedule search of gbs_autotune, for a ragged batch):
    times gbs_cumulants_batched on this batch under candidate schedules -- every
    CTA shape allowed for the precision and the largest M (512 x 1, 256 x 2 when
-   M <= 577; refined also 640 x 1 and 256 x 3 when M <= 577) at the default
+   M <= 577; refined also 640 x 1, 256 x 3 when M <= 577, and 768 x 1) at the default
    grain and batch size, then items per CTA slot (1, 2, 4, 8) x children per
    batch (16, 64) for the fastest shape -- records the fastest for this batch
    shape (multiset of (M, kmax), device, precision; persisted like gbs_autotune's
@@ -295,7 +320,8 @@ int gbs_batched_autotune(const gbs_instance *inst, int n, int precision, void *w
    gbs_batched_autotune in this process): schedule_out[5] (host) = {CTA shape
    (0: 512 threads x 1 per SM, 1: 256 x 2, 2: 640 x 1, 3: 256 x 3), threads per
    CTA, CTAs in the launch, items per CTA slot, children per shared-memory
-   batch}. Returns GBS_OK or GBS_ERR_INVALID_ARG (no plan). */
+   batch}, shape 4 being 768 threads x 1. Returns GBS_OK or GBS_ERR_INVALID_ARG
+   (no plan). */
 int gbs_batched_schedule(const void *workspace, int *schedule_out);
 
 /* ---------------------------------------------------------------- gradients */

@@ -68,6 +68,9 @@ def lib() -> ctypes.CDLL:
     L.gbs_autotune.restype = i32
     L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
     L.gbs_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float)]; L.gbs_timing_read.restype = i32
+    L.gbs_timing_read_backward.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    L.gbs_timing_read_backward.restype = i32
+    L.gbs_pipe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), vp, vp]; L.gbs_pipe_peaks.restype = i32
     L.gbs_backward_workspace_bytes.argtypes = [i32, i32]; L.gbs_backward_workspace_bytes.restype = sz
     L.gbs_cumulants_backward.argtypes = [vp, i32, i32, vp, vp, vp, sz, vp]; L.gbs_cumulants_backward.restype = i32
     L.gbs_covariance.argtypes = [vp, vp, vp, vp, i32, vp, vp]; L.gbs_covariance.restype = i32
@@ -458,7 +461,7 @@ class Batch:
         """The batched kernel's schedule in this plan (gbs_batched_schedule)."""
         arr = (ctypes.c_int * 5)()
         _check(lib().gbs_batched_schedule(_vp(self.ws), arr))
-        shape = {0: "512x1", 1: "256x2", 2: "640x1", 3: "256x3"}.get(arr[0], str(arr[0]))
+        shape = {0: "512x1", 1: "256x2", 2: "640x1", 3: "256x3", 4: "768x1"}.get(arr[0], str(arr[0]))
         return {"cta_shape": shape, "threads": arr[1], "ctas": arr[2], "grain": arr[3], "children_per_batch": arr[4]}
 
     def run(self, check=False):
@@ -513,6 +516,28 @@ def timing_read() -> list[float]:
     """[pack, order 1, .., order 5] kernel milliseconds of the most recent timed call."""
     arr = (ctypes.c_float * 6)()
     _check(lib().gbs_timing_read(arr))
+    return list(arr)
+
+
+PIPE_PEAKS_SCRATCH = 65536
+
+
+def pipe_peaks(device=None) -> dict:
+    """Measured sustained FMA throughput of the FP64 and FP32 pipes (gbs_pipe_peaks)."""
+    dev = torch.device(device or "cuda")
+    scratch = torch.empty(PIPE_PEAKS_SCRATCH, dtype=torch.uint8, device=dev)
+    out = (ctypes.c_double * 6)()
+    st = torch.cuda.current_stream(dev)
+    _check(lib().gbs_pipe_peaks(out, _vp(scratch), ctypes.c_void_p(st.cuda_stream)))
+    return {"fp64_flops": out[0], "fp32_flops": out[1], "fp64_fma_per_clk_per_sm": out[2],
+            "fp32_fma_per_clk_per_sm": out[3], "sm_mhz_fp64_probe": out[4], "sm_mhz_fp32_probe": out[5]}
+
+
+def timing_read_backward() -> list[float]:
+    """[P0 recomputation, h table, dL/dP0 gather, dL/dV scatter] milliseconds of the
+    most recent timed gbs_cumulants_backward call."""
+    arr = (ctypes.c_float * 4)()
+    _check(lib().gbs_timing_read_backward(arr))
     return list(arr)
 
 

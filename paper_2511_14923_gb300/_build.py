@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbs.so")
-SOURCES = ["gbs_api.cu", "gbs_fwd.cu", "gbs_batch.cu", "gbs_bwd.cu", "gbs_tune.cu", "gbs_noalloc.cu", "gbs_disp.cu", "gbs_sampler.cu"]
+SOURCES = ["gbs_api.cu", "gbs_fwd.cu", "gbs_batch.cu", "gbs_bwd.cu", "gbs_tune.cu", "gbs_noalloc.cu", "gbs_disp.cu", "gbs_sampler.cu", "gbs_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

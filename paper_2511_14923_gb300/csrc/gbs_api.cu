@@ -20,6 +20,10 @@ bool g_timing = false;
 bool g_timing_used = false;
 cudaEvent_t g_ev[GBS_MAX_ORDER + 2];
 bool g_ev_ready = false;
+// Backward-pass events: ev[0] before the P0 recomputation, ev[i] after phase i.
+bool g_bwd_timing_used = false;
+cudaEvent_t g_bev[5];
+bool g_bev_ready = false;
 
 int fail(int code, const char *fmt, ...) {
     va_list ap;
@@ -102,6 +106,7 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
     a.precision = precision;
     a.A = reinterpret_cast<double *>(w + L.A_off);
     a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
+    a.p0f = reinterpret_cast<float *>(w + L.p0f_off);
     a.p0 = (mode == gbs::MODE_P0) ? out : reinterpret_cast<double *>(w + L.p0_off);
     a.out = out;
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);
@@ -204,6 +209,20 @@ int gbs_timing_read(float *ms_out) {
     return ok();
 }
 
+int gbs_timing_read_backward(float *ms_out) {
+    if (!ms_out) return fail(GBS_ERR_INVALID_ARG, "NULL output");
+    if (!g_bev_ready || !g_bwd_timing_used) return fail(GBS_ERR_INVALID_ARG, "no timed backward call has been made");
+    cudaError_t e = cudaEventSynchronize(g_bev[4]);
+    if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 4; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, g_bev[i], g_bev[i + 1]);
+        if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
+        ms_out[i] = ms;
+    }
+    return ok();
+}
+
 int gbs_stream_status(const void *workspace, void *cuda_stream) {
     if (!workspace) return fail(GBS_ERR_INVALID_ARG, "NULL workspace");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -269,6 +288,17 @@ int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_
     b.h = reinterpret_cast<double *>(w + L.h_off);
     b.gp0 = reinterpret_cast<double *>(w + L.gp0_off);
     b.inv = reinterpret_cast<double *>(w + L.inv_off);
+    b.ev = nullptr;
+    if (g_timing) {
+        if (!g_bev_ready) {
+            for (auto &ev : g_bev)
+                if ((e = cudaEventCreate(&ev)) != cudaSuccess)
+                    return fail(GBS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+            g_bev_ready = true;
+        }
+        b.ev = g_bev;
+        g_bwd_timing_used = true;
+    }
     e = gbs::launch_backward(b, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
     return ok();
@@ -400,6 +430,7 @@ int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precis
     a.precision = precision;
     a.A = reinterpret_cast<double *>(w + L.A_off);
     a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
+    a.p0f = reinterpret_cast<float *>(w + L.p0f_off);
     a.p0 = reinterpret_cast<double *>(w + L.p0_off);
     a.out = kappa_out;
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);

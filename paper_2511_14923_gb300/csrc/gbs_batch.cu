@@ -44,6 +44,7 @@ struct InstDev {
     const double *V;
     double *out;
     double *A;
+    float *p0f;  // P0({x}) as float pairs (refined path)
     double *p0;
     int M, kmax;
     uint32_t c4off[2];   // offsets into the c4-prefix pool for orders 4 and 5
@@ -135,6 +136,8 @@ void build_plan(const gbs_instance *in, int n, int precision, int sms, int grid,
         I.kmax = x.kmax;
         I.A = reinterpret_cast<double *>(base + off);  // FP64 blocks, then the float-pair copy
         off = a256(off + 2 * sizeof(double) * 4 * (size_t)x.M * x.M);
+        I.p0f = reinterpret_cast<float *>(base + off);
+        off = a256(off + 2 * sizeof(float) * (size_t)x.M);
         I.p0 = reinterpret_cast<double *>(base + off);
         off = a256(off + sizeof(double) * (x.kmax > 1 ? order_offset(x.M, x.kmax) : 0));
         for (int d = 4; d <= 5; ++d) {
@@ -184,6 +187,7 @@ __device__ __forceinline__ FwdArgs inst_args(const InstDev &I, unsigned *status,
     a.precision = precision;
     a.A = I.A;
     a.Af = reinterpret_cast<float *>(I.A + 4 * (size_t)I.M * I.M);
+    a.p0f = I.p0f;
     a.p0 = I.p0;
     a.out = I.out;
     a.status = status;
@@ -296,7 +300,8 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(char *ws) {
 }
 
 // Kernel of one CTA shape (variant numbering as for the single-instance
-// schedules: 0 = 512 x 1, 1 = 256 x 2, refined only 2 = 640 x 1, 3 = 256 x 3).
+// schedules: 0 = 512 x 1, 1 = 256 x 2, refined only 2 = 640 x 1, 3 = 256 x 3,
+// 4 = 768 x 1 with a 2048-entry x area).
 struct KernelInfo {
     void *fn;
     int nt, xc;
@@ -309,7 +314,7 @@ KernelInfo kinfo() {
 }
 
 bool variant_ok(int precision, int variant, int maxM) {
-    if (variant < 0 || variant > 3) return false;
+    if (variant < 0 || variant >= kNumVariants) return false;
     if (precision == 0 && variant >= 2) return false;
     if ((variant == 1 || variant == 3) && maxM > kVariant1MaxM) return false;
     return true;
@@ -321,6 +326,7 @@ KernelInfo kernel_for(int precision, int variant) {
         case 1: return kinfo<1, 256, 576, 2>();
         case 2: return kinfo<1, 640, XCAP, 1>();
         case 3: return kinfo<1, 256, 576, 3>();
+        case 4: return kinfo<1, 768, kWideXC, 1>();
         default: return kinfo<1, TREE_THREADS, XCAP, 1>();
     }
 }
@@ -469,7 +475,7 @@ int batched_autotune(const gbs_instance *inst, int n, int precision, char *ws, s
     };
     // coordinate search: the CTA shape at the default grain and batch size, then
     // grain x children per batch for the fastest shape
-    for (int v = 0; v <= 3 && rc == GBS_OK; ++v)
+    for (int v = 0; v < kNumVariants && rc == GBS_OK; ++v)
         if (variant_ok(precision, v, maxM)) time_cfg(TreeCfg{kDefaultCfg.grain, kDefaultCfg.ccap, v});
     const int vbest = best.variant;
     for (int grain : {1, 2, 4, 8})

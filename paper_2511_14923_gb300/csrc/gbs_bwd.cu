@@ -461,18 +461,24 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
     const int M = a.M, K = a.kmax;
     const Offsets o = make_offsets(M);
     cudaError_t e;
+    auto mark = [&](int i) {
+        if (a.ev) cudaEventRecord(a.ev[i], st);
+    };
+    mark(0);
     // 1. P0 table of every order (forward kernels, FP64)
     FwdArgs f = a.fwd;
     f.mode = MODE_P0;
     f.precision = GBS_FP64;
     f.p0 = f.out = a.p0;
     if ((e = launch_forward(f, st)) != cudaSuccess) return e;
+    mark(1);
     // 2. h table, orders 1..kmax-1
     for (int r = 1; r < K; ++r) {
         const uint64_t n = binom(M, r);
         h_kernel<<<(unsigned)((n + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(M, r, o, a.p0, a.h);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    mark(2);
     // 3. gP0 by gathering over supersets (one group per subset B)
     for (int b = 1; b <= K; ++b) {
         const uint64_t n = binom(M, b);
@@ -492,6 +498,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    mark(3);
     // 4. grad_V: order 1 directly, higher orders per prefix T'
     const size_t n2 = 2 * (size_t)M;
     if ((e = cudaMemsetAsync(a.gV, 0, sizeof(double) * n2 * n2, st)) != cudaSuccess) return e;
@@ -519,6 +526,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
     }
     mirror_kernel<<<(unsigned)((n2 * n2 + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>((int)n2, a.gV);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    mark(4);
     return cudaSuccess;
 }
 

@@ -19,6 +19,7 @@ struct BwdArgs {
     double *h;          // inverse-moment table, orders < kmax (workspace)
     double *gp0;        // dL/dP0 table (workspace)
     double *inv;        // inverses of A_{T'} for one prefix order (workspace)
+    cudaEvent_t *ev;    // 5 timing events around the phases (P0, h, dL/dP0, dL/dV), or nullptr
 };
 
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st);

@@ -57,6 +57,8 @@ WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm) {
     off = align256(off + 256);
     w.A_off = off;  // FP64 blocks, then the float-pair copy
     off = align256(off + 2 * sizeof(double) * 4 * (size_t)M * M);
+    w.p0f_off = off;  // P0({x}) as float pairs
+    off = align256(off + 2 * sizeof(float) * (size_t)M);
     w.p0_off = off;
     const uint64_t np0 = kmax > 1 ? order_offset(M, kmax) : 0;  // orders 1..kmax-1
     off = align256(off + sizeof(double) * (size_t)np0);

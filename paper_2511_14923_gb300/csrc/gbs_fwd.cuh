@@ -19,6 +19,7 @@ struct FwdArgs {
     int M, kmax, mode, precision;
     double *A;            // packed 2x2 blocks of (V+I)/2, M*M*4 doubles (workspace)
     float *Af;            // the same blocks as float pairs (hi x4, lo x4), refined path (workspace)
+    float *p0f;           // P0({x}) as float pairs (hi, lo) per mode, refined path (workspace; may be null)
     double *p0;           // P0 table: the output for MODE_P0, a workspace table (orders < kmax) otherwise
     double *out;          // mu or kappa table (MODE_MU / MODE_KAPPA); equals p0 for MODE_P0
     unsigned *status;     // status word (workspace)
@@ -30,7 +31,7 @@ struct FwdArgs {
     cudaEvent_t *ev;      // GBS_MAX_ORDER + 2 timing events, or nullptr
     // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
     // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
-    // only: 2: 640 x 1, 3: 256 x 3)
+    // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area)
     int grain, ccap, variant;
 };
 
@@ -41,10 +42,14 @@ struct TreeCfg {
 constexpr TreeCfg kDefaultCfg{2, 64, 0};
 // Largest M the 256-thread variant accepts (its shared x-entry area holds 576 modes).
 constexpr int kVariant1MaxM = 577;
+// x-entries per batch of the 768-thread refined variant (one CTA per SM).
+constexpr int kWideXC = 2048;
+// Number of CTA shapes (variants 0..kNumVariants-1).
+constexpr int kNumVariants = 5;
 
 // Workspace layout, shared by the size query and the launcher.
 struct WsLayout {
-    size_t status_off, A_off, p0_off, scratch_off, total;
+    size_t status_off, A_off, p0f_off, p0_off, scratch_off, total;
     size_t slot_doubles;
     int slots;
 };

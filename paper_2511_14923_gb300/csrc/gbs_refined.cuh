@@ -110,10 +110,11 @@ __device__ __forceinline__ void eft_sub_dfprod(EftAcc &a, float xh, float xl, fl
 
 __device__ __forceinline__ float eft_val(const EftAcc &a) { return __fadd_rn(a.s, a.e); }
 
-// Refined det(Sch_j)^{-1/2} times P0(S'); ok = false if the FP32 factorisation
-// meets a non-positive pivot.
-__device__ __forceinline__ double refined_leaf_p0(double P0Sp, const DFBlk &S, const DFBlk &z2, const DFBlk &zj,
-                                                  const DFSym &D, const F32Piv &pv, bool &ok) {
+// Refined det(Sch_j)^{-1/2} = r0 (1 + eta), r0 an FP32 reciprocal and eta its
+// correction (refinement and reciprocal residual); ok = false if the FP32
+// factorisation meets a non-positive pivot.
+__device__ __forceinline__ void refined_leaf_factor(const DFBlk &S, const DFBlk &z2, const DFBlk &zj, const DFSym &D,
+                                                    const F32Piv &pv, float &r0_out, float &eta_out, bool &ok) {
     // X ~ S - z2^T zj in FP32 (only feeds the FP32 factorisation)
     const float x00 = __fmaf_rn(-z2.h10, zj.h10, __fmaf_rn(-z2.h00, zj.h00, S.h00));
     const float x01 = __fmaf_rn(-z2.h10, zj.h11, __fmaf_rn(-z2.h00, zj.h01, S.h01));
@@ -202,8 +203,37 @@ __device__ __forceinline__ double refined_leaf_p0(double P0Sp, const DFBlk &S, c
     const float r0 = __frcp_rn(qh);
     const float eps = -__fmaf_rn(ql, r0, __fmaf_rn(qh, r0, -1.f));
     const float eta = __fmaf_rn(eps, eps, eps) + delta * __fmaf_rn(0.125f, delta, __fmaf_rn(-0.5f, eps, -0.5f));
+    r0_out = r0;
+    eta_out = eta;
+}
+
+// P0(S) = P0(S') r0 (1 + eta): two FP64 operations.
+__device__ __forceinline__ double refined_leaf_p0(double P0Sp, const DFBlk &S, const DFBlk &z2, const DFBlk &zj,
+                                                  const DFSym &D, const F32Piv &pv, bool &ok) {
+    float r0, eta;
+    refined_leaf_factor(S, z2, zj, D, pv, r0, eta, ok);
     const double u = P0Sp * f2d_bits(r0);
     return fma(u, f2d_bits(eta), u);
+}
+
+// +-(P0(S) - P0({j}) P0(S')) = +-P0(S') (r0 (1 + eta) - p) (minus when NEG), the
+// leading term of the cumulant recursion when P0(S) itself is not stored, with
+// p = P0({j}) given as an FP32 pair (ph + pl). The difference
+// w = r0 - ph + r0 eta - pl is formed on the FP32 pipe as an unevaluated pair
+// (two-sum of r0 - ph, which is exact when they are close, plus the exact
+// product r0 eta), so only the two products with P0(S') run in FP64: one FP64
+// instruction fewer than forming P0(S) first. The sign goes into the FP32 bits.
+template <bool NEG>
+__device__ __forceinline__ double refined_lead_term(double P0Sp, float r0, float eta, float ph, float pl) {
+    const float s = __fadd_rn(r0, -ph);
+    const float bb = __fsub_rn(s, r0);
+    const float e1 = __fadd_rn(__fsub_rn(r0, __fsub_rn(s, bb)), __fsub_rn(-ph, bb));
+    const float pr = r0 * eta;
+    const float qr = __fmaf_rn(r0, eta, -pr);
+    const float lo = __fadd_rn(__fadd_rn(e1, -pl), __fadd_rn(pr, qr));
+    const unsigned flip = NEG ? 0x80000000u : 0u;
+    return fma(P0Sp, f2d_bits(__uint_as_float(__float_as_uint(lo) ^ flip)),
+               P0Sp * f2d_bits(__uint_as_float(__float_as_uint(s) ^ flip)));
 }
 
 }  // namespace gbs

@@ -47,6 +47,13 @@ __device__ __forceinline__ void child_bases(const int *P, int M, uint64_t *baseJ
     }
 }
 
+template <int NP, int MODE>
+__host__ __device__ constexpr double lead_sign();
+template <int NP, int MODE>
+__device__ __forceinline__ double combine_tail(double acc, int j, int c2, uint32_t t, const uint64_t *baseJ,
+                                               const uint64_t *baseT, const double *p0R,
+                                               const double *__restrict__ p0tab, const double *__restrict__ outtab);
+
 // Mode-specific value of the leaf S = {j, c2} + P (|P| = NP) given P0(S).
 // p0R[R] = P0(R) for nonempty R subset of P.
 template <int NP, int MODE>
@@ -81,22 +88,45 @@ __device__ __forceinline__ double combine(double P0S, int j, int c2, uint32_t t,
         return acc;
     }
     // MODE_KAPPA: kt(S) = (-1)^d [bracket];  MODE_SPINK: kappa(S) = (-2)^d kt(S) = 2^d [bracket],
-    // with the lower-order table holding kappa = (-2)^{|Q|} kt (exact power-of-two scalings)
-    double acc = fma(-p0tab[j], p0tab[baseJ[PALL] + c2], P0S);
+    // with the lower-order table holding kappa = (-2)^{|Q|} kt (exact power-of-two scalings).
+    // The bracket is accumulated already multiplied by lead_sign (the sign of the
+    // order for MODE_KAPPA), which every FMA absorbs as an operand negation.
+    constexpr double sd = lead_sign<NP, MODE>();
+    return combine_tail<NP, MODE>(fma(-sd * p0tab[j], p0tab[baseJ[PALL] + c2], sd * P0S), j, c2, t, baseJ, baseT,
+                                  p0R, p0tab, outtab);
+}
+
+// Sign carried by the accumulator of the cumulant recursion: (-1)^d for the
+// click cumulant (d = NP + 2), + for the spin cumulant.
+template <int NP, int MODE>
+__host__ __device__ constexpr double lead_sign() {
+    return (MODE == MODE_KAPPA && ((NP + 2) & 1)) ? -1.0 : 1.0;
+}
+
+// The cumulant recursion (MODE_KAPPA, MODE_SPINK) after its leading term
+// acc = lead_sign (P0(S) - P0({j}) P0(S')): the 2^{d-1} - 2 products with
+// lower-order cumulants (signs folded into each FMA), then, for the spin
+// cumulant, the power of two.
+template <int NP, int MODE>
+__device__ __forceinline__ double combine_tail(double acc, int j, int c2, uint32_t t, const uint64_t *baseJ,
+                                               const uint64_t *baseT, const double *p0R,
+                                               const double *__restrict__ p0tab, const double *__restrict__ outtab) {
+    constexpr int PALL = (1 << NP) - 1;
+    constexpr double sd = lead_sign<NP, MODE>();
 #pragma unroll
     for (int q = 1; q <= PALL; ++q) {
-        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? -1.0 : 1.0)
+        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? -sd : sd)
                                                : -1.0 / (double)(2 << __popc(q));  // -2^{-(|R|+1)}, R = Q
         acc = fma(sg * outtab[baseJ[q] + j], p0tab[baseJ[PALL ^ q] + c2], acc);
     }
 #pragma unroll
     for (int q = 0; q < PALL; ++q) {
-        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? 1.0 : -1.0)
+        const double sg = (MODE == MODE_KAPPA) ? ((__popc(q) & 1) ? sd : -sd)
                                                : -1.0 / (double)(4 << __popc(q));  // R = Q + {c2}
         acc = fma(sg * outtab[baseT[q] + t], p0R[PALL ^ q], acc);
     }
     if (MODE == MODE_SPINK) return acc * (double)(1 << (NP + 2));
-    return ((NP + 2) & 1) ? -acc : acc;
+    return acc;
 }
 
 // ---------------------------------------------------------------- small kernels
@@ -140,6 +170,7 @@ __device__ __forceinline__ void order1_entry(const FwdArgs &a, int j, bool write
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
     }
     if (write_p0) a.p0[j] = P0;
+    if (a.p0f && a.precision == 1) split_df(P0, a.p0f[2 * j], a.p0f[2 * j + 1]);
     // mu({j}) = kt({j}) = 1 - P0({j});  c({j}) = kappa({j}) = 2 P0({j}) - 1
     if (MODE == MODE_MU || MODE == MODE_KAPPA) a.out[j] = 1.0 - P0;
     if (MODE == MODE_SPINC || MODE == MODE_SPINK) a.out[j] = fma(2.0, P0, -1.0);
@@ -586,61 +617,81 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
             }
         }
         __syncthreads();
-        // leaves (c2, j), j < c2 < c3, flattened over the batch
-        const uint32_t L = sh.lpref[nb];
-        for (uint32_t g = tid; g < L; g += NT) {
-            int lo2 = 0, hi2 = nb;
-            while (hi2 - lo2 > 1) {
-                const int mid = (lo2 + hi2) >> 1;
-                if (sh.lpref[mid] <= g) lo2 = mid;
-                else hi2 = mid;
-            }
-            const int b = lo2;
-            const uint32_t t = g - sh.lpref[b];
+        // leaves (c2, j), j < c2 < c3: pairs t = C(c2, 2) + j on the outer loop and
+        // the batch's children (c3 decreasing with b) inside, so each 2x2 block of
+        // the slot is read once per batch instead of once per child
+        const uint32_t L0 = (uint32_t)binom2(sh.c3[0]);
+        for (uint32_t t = tid; t < L0; t += NT) {
             int c2, j;
             pair_decode(t, c2, j);
-            const int xo = sh.xoff[b];
-            const int e2 = xo + c2, ej = xo + j;
-            const uint64_t *bJ = sh.baseJ[b];
-            const uint64_t *bT = sh.baseT[b];
-            const double P0Sp = a.p0[bJ[PALL] + c2];
-            double P0;
-            bool ok;
-            if (PREC == 0) {
-                const Blk z2{xe[0][e2], xe[1][e2], xe[2][e2], xe[3][e2]};
-                const Blk zj{xe[0][ej], xe[1][ej], xe[2][ej], xe[3][ej]};
-                const LInv m2{xe[7][e2], xe[8][e2], xe[9][e2]};
-                const Sym dj{xe[4][ej], xe[5][ej], xe[6][ej]};
-                const Blk X = blk_sub_cross(load_blk(slot + 4 * (size_t)t), z2, zj);
-                const Blk w = lmul(m2, X);
-                const Sym sch = sym_sub_gram(dj, w);
-                const double det2 = det_sym(sch);
-                const double rs = rsqrt(det2);
-                P0 = P0Sp * rs;
-                if constexpr (DISP) {
-                    const Vec2 r = sub_wtg(Vec2{xe[10][ej], xe[11][ej]}, w, Vec2{xe[12][e2], xe[13][e2]});
-                    P0 *= exp(-quad_inv(sch, rs * rs, r));
-                }
-                ok = det2 > 0.0;
+            Blk S64{0, 0, 0, 0};
+            DFBlk Sdf{};
+            if constexpr (PREC == 0) {
+                S64 = load_blk(slot + 4 * (size_t)t);
             } else {
                 const float4 *fs = reinterpret_cast<const float4 *>(slot) + 2 * (size_t)t;
                 const float4 sh4 = fs[0], sl4 = fs[1];
-                const DFBlk S{sh4.x, sh4.y, sh4.z, sh4.w, sl4.x, sl4.y, sl4.z, sl4.w};
-                const DFBlk z2{xf[0][e2], xf[1][e2], xf[2][e2], xf[3][e2], xf[4][e2], xf[5][e2], xf[6][e2], xf[7][e2]};
-                const DFBlk zj{xf[0][ej], xf[1][ej], xf[2][ej], xf[3][ej], xf[4][ej], xf[5][ej], xf[6][ej], xf[7][ej]};
-                const DFSym dj{xf[8][ej], xf[9][ej], xf[10][ej], xf[11][ej], xf[12][ej], xf[13][ej]};
-                const F32Piv pv{xf[14][e2], xf[15][e2], xf[16][e2], xf[17][e2], xf[18][e2],
-                                xf[19][e2], xf[20][e2], xf[21][e2], xf[22][e2]};
-                P0 = refined_leaf_p0(P0Sp, S, z2, zj, dj, pv, ok);
+                Sdf = DFBlk{sh4.x, sh4.y, sh4.z, sh4.w, sl4.x, sl4.y, sl4.z, sl4.w};
             }
-            if (!ok) {
-                flag_status(a.status, ST_NOT_POSDEF);
-                P0 = __longlong_as_double(0x7ff8000000000000ULL);
+            for (int b = 0; b < nb && c2 < sh.c3[b]; ++b) {
+                const int xo = sh.xoff[b];
+                const int e2 = xo + c2, ej = xo + j;
+                const uint64_t *bJ = sh.baseJ[b];
+                const uint64_t *bT = sh.baseT[b];
+                const double P0Sp = a.p0[bJ[PALL] + c2];
+                double P0;
+                bool ok;
+                if constexpr (PREC == 0) {
+                    const Blk z2{xe[0][e2], xe[1][e2], xe[2][e2], xe[3][e2]};
+                    const Blk zj{xe[0][ej], xe[1][ej], xe[2][ej], xe[3][ej]};
+                    const LInv m2{xe[7][e2], xe[8][e2], xe[9][e2]};
+                    const Sym dj{xe[4][ej], xe[5][ej], xe[6][ej]};
+                    const Blk X = blk_sub_cross(S64, z2, zj);
+                    const Blk w = lmul(m2, X);
+                    const Sym sch = sym_sub_gram(dj, w);
+                    const double det2 = det_sym(sch);
+                    const double rs = rsqrt(det2);
+                    P0 = P0Sp * rs;
+                    if constexpr (DISP) {
+                        const Vec2 r = sub_wtg(Vec2{xe[10][ej], xe[11][ej]}, w, Vec2{xe[12][e2], xe[13][e2]});
+                        P0 *= exp(-quad_inv(sch, rs * rs, r));
+                    }
+                    ok = det2 > 0.0;
+                } else {
+                    const DFBlk z2{xf[0][e2], xf[1][e2], xf[2][e2], xf[3][e2], xf[4][e2], xf[5][e2], xf[6][e2], xf[7][e2]};
+                    const DFBlk zj{xf[0][ej], xf[1][ej], xf[2][ej], xf[3][ej], xf[4][ej], xf[5][ej], xf[6][ej], xf[7][ej]};
+                    const DFSym dj{xf[8][ej], xf[9][ej], xf[10][ej], xf[11][ej], xf[12][ej], xf[13][ej]};
+                    const F32Piv pv{xf[14][e2], xf[15][e2], xf[16][e2], xf[17][e2], xf[18][e2],
+                                    xf[19][e2], xf[20][e2], xf[21][e2], xf[22][e2]};
+                    if constexpr (MODE == MODE_KAPPA || MODE == MODE_SPINK) {
+                        if (!write_p0 && a.p0f) {
+                            // P0(S) is not stored: its product with P0(S') folds into the
+                            // recursion's leading term (16 FP64 instructions per entry)
+                            float r0, eta;
+                            refined_leaf_factor(Sdf, z2, zj, dj, pv, r0, eta, ok);
+                            const float2 pj = reinterpret_cast<const float2 *>(a.p0f)[j];
+                            double v = combine_tail<NP, MODE>(
+                                refined_lead_term<(lead_sign<NP, MODE>() < 0)>(P0Sp, r0, eta, pj.x, pj.y), j, c2, t,
+                                bJ, bT, sh.p0R[b], a.p0, a.out);
+                            if (!ok) {
+                                flag_status(a.status, ST_NOT_POSDEF);
+                                v = __longlong_as_double(0x7ff8000000000000ULL);
+                            }
+                            a.out[bT[PALL] + t] = v;
+                            continue;
+                        }
+                    }
+                    P0 = refined_leaf_p0(P0Sp, Sdf, z2, zj, dj, pv, ok);
+                }
+                if (!ok) {
+                    flag_status(a.status, ST_NOT_POSDEF);
+                    P0 = __longlong_as_double(0x7ff8000000000000ULL);
+                }
+                const double v = combine<NP, MODE>(P0, j, c2, t, bJ, bT, sh.p0R[b], a.p0, a.out);
+                const uint64_t idx = bT[PALL] + t;
+                if (write_p0) a.p0[idx] = P0;
+                if (MODE != MODE_P0) a.out[idx] = v;
             }
-            const double v = combine<NP, MODE>(P0, j, c2, t, bJ, bT, sh.p0R[b], a.p0, a.out);
-            const uint64_t idx = bT[PALL] + t;
-            if (write_p0) a.p0[idx] = P0;
-            if (MODE != MODE_P0) a.out[idx] = v;
         }
         __syncthreads();
         k0 += nb;

@@ -5,7 +5,8 @@
 //   grain   items per CTA slot (subtree granularity: 1, 2, 4, 8),
 //   ccap    children per shared-memory batch (16 or 64),
 //   variant CTA shape: 512 threads x 1 per SM; 256 x 2 per SM (M <= 577); and for
-//           the refined path 640 x 1, or 256 x 3 (M <= 577).
+//           the refined path 640 x 1, 256 x 3 (M <= 577), or 768 x 1 with room
+//           for more children per batch.
 // Results live in a process-wide table consulted by every forward call; if the
 // environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
 // it on first use and rewritten after each tuning run (a JSON array of objects).
@@ -117,13 +118,13 @@ void load_locked() {
             if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "precision", prec) &&
                 read_int(p, end, "n", nb) && read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
                 read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
-                variant >= 0 && variant <= 3)
+                variant >= 0 && variant < kNumVariants)
                 g_btable[BKey{cc, sms, prec, sig}] = BEntry{TreeCfg{grain, ccap, variant}, -1.f, nb};
         } else if (read_int(p, end, "cc", cc) && read_int(p, end, "sms", sms) && read_int(p, end, "M", M) &&
             read_int(p, end, "kmax", kmax) && read_int(p, end, "precision", prec) &&
             read_int(p, end, "grain", grain) && read_int(p, end, "ccap", ccap) &&
             read_int(p, end, "variant", variant) && grain >= 1 && grain <= 64 && ccap >= 1 && ccap <= 64 &&
-            variant >= 0 && variant <= 3) {
+            variant >= 0 && variant < kNumVariants) {
             g_table[Key{cc, sms, M, kmax, prec}] = Entry{TreeCfg{grain, ccap, variant}, -1.f};
         }
         p = end + 1;
@@ -199,7 +200,7 @@ void record_batch_cfg(int sms, const gbs_instance *inst, int n, int precision, c
 
 int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tried) {
     std::vector<TreeCfg> cand;
-    for (int variant = 0; variant <= (a.precision == 1 ? 3 : 1); ++variant) {
+    for (int variant = 0; variant <= (a.precision == 1 ? kNumVariants - 1 : 1); ++variant) {
         if ((variant == 1 || variant == 3) && a.M > kVariant1MaxM) continue;
         for (int grain : {1, 2, 4, 8})
             for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, ccap, variant});
