@@ -198,6 +198,38 @@ typedef enum {
 int gbs_displaced_tables(const double *V, const double *mean, int M, int kmax, int table, double *out,
                          void *workspace, size_t ws_bytes, void *cuda_stream);
 
+/* ---------------------------------------------------------------- sharded tables (rank ranges) */
+
+/* Tables too large for one GPU (e.g. M = 1024, kmax = 4: 4.5e10 entries, 360 GB
+   in FP64; the paper's scaling toward thousands of modes, Sec. "Cost estimation
+   and scaling", and the 1152-mode state of Sec. "High-brightness results for
+   Jiuzhang 3.0") are filled in slices of their top order. The order-kmax subsets
+   whose largest mode c_kmax lies in [c_lo, c_hi) have the contiguous colex ranks
+   [C(c_lo, kmax), C(c_hi, kmax)), so a slice is one contiguous block of the
+   order-kmax group; slices over consecutive ranges, concatenated, are that group.
+
+   gbs_table_range fills out[0 .. gbs_range_entries(M, kmax, c_lo, c_hi)) with the
+   entries of `table` (a gbs_table value: P0, click moment, click cumulant, spin
+   correlator, spin cumulant) for those subsets: out[r - C(c_lo, kmax)] is the
+   entry of colex rank r. The lower orders, which the recursions read, are
+   computed in full inside the workspace (gbs_range_workspace_bytes; it holds
+   them besides what gbs_workspace_bytes covers) and not returned: take them
+   from any whole-table call with kmax - 1. The values equal those of the
+   whole-table call bit for bit. Requires 0 <= c_lo <= c_hi <= M; other errors as
+   for the whole-table calls. */
+size_t gbs_range_workspace_bytes(int M, int kmax, int precision);
+uint64_t gbs_range_entries(int M, int kmax, int c_lo, int c_hi);
+int gbs_table_range(const double *V, int M, int kmax, int table, int c_lo, int c_hi, double *out, int precision,
+                    void *workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Cost-balanced split of the top elements into n_parts ranges: bounds_out[0] = 0,
+   bounds_out[n_parts] = M, and part i = [bounds_out[i], bounds_out[i + 1]) holds
+   about C(M, kmax) / n_parts entries (each boundary is the smallest c with
+   C(c, kmax) >= i C(M, kmax) / n_parts; the entries of the prefix-tree kernels
+   cost alike, so equal counts are equal work). Host only. bounds_out: n_parts + 1
+   ints. Returns GBS_OK or GBS_ERR_INVALID_ARG (n_parts outside [1, M]). */
+int gbs_range_split(int M, int kmax, int n_parts, int *bounds_out);
+
 /* ---------------------------------------------------------------- stage 2: sampler */
 
 /* Arithmetic of the sampler's tables and sums. */
@@ -389,9 +421,18 @@ int gbs_covariance_backward(const double *U_re, const double *U_im, const double
    call's contents (the status word and work counters are cleared at the start
    of every call). Calls whose work may overlap on the GPU -- on different
    streams, or from different host threads -- race on the array; serialise
-   them (one stream). Device-side errors leave NaN in the affected entries.
+   them (one stream). Device-side errors leave NaN in the affected entries and
+   set the status word that gbs_noalloc_status reads.
    Returns GBS_OK, GBS_ERR_INVALID_ARG, GBS_ERR_WORKSPACE or GBS_ERR_CUDA. */
 int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *kappa_out, void *cuda_stream);
+
+/* Device status of the allocation-free calls on the current device, the
+   counterpart of gbs_stream_status for gbs_cumulants_noalloc, whose caller holds
+   no workspace to pass: synchronises cuda_stream, then reads the status word kept
+   in the library's fixed scratch array (allocating nothing) and returns GBS_OK,
+   GBS_ERR_NOT_POSDEF or another device status, as gbs_stream_status does. The
+   word is cleared by the next gbs_cumulants_noalloc call on that device. */
+int gbs_noalloc_status(void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -93,6 +93,12 @@ def lib() -> ctypes.CDLL:
     L.gbs_sample.restype = i32
     L.gbs_displaced_tables.argtypes = [vp, vp, i32, i32, i32, vp, vp, sz, vp]
     L.gbs_displaced_tables.restype = i32
+    L.gbs_range_workspace_bytes.argtypes = [i32, i32, i32]; L.gbs_range_workspace_bytes.restype = sz
+    L.gbs_range_entries.argtypes = [i32, i32, i32, i32]; L.gbs_range_entries.restype = u64
+    L.gbs_range_split.argtypes = [i32, i32, i32, ctypes.POINTER(i32)]; L.gbs_range_split.restype = i32
+    L.gbs_table_range.argtypes = [vp, i32, i32, i32, i32, i32, vp, i32, vp, sz, vp]
+    L.gbs_table_range.restype = i32
+    L.gbs_noalloc_status.argtypes = [vp]; L.gbs_noalloc_status.restype = i32
     _lib = L
     return L
 
@@ -270,6 +276,45 @@ def displaced_tables(V, mean, kmax, table="kappa", out=None, workspace=None, che
     return out
 
 
+def range_split(M: int, kmax: int, n_parts: int) -> list[int]:
+    """Cost-balanced top-element bounds [0 = b_0 <= .. <= b_n = M] of n_parts slices
+    of the order-kmax group (gbs_range_split)."""
+    arr = (ctypes.c_int * (n_parts + 1))()
+    _check(lib().gbs_range_split(M, kmax, n_parts, arr))
+    return list(arr)
+
+
+def range_entries(M: int, kmax: int, c_lo: int, c_hi: int) -> int:
+    return int(lib().gbs_range_entries(M, kmax, c_lo, c_hi))
+
+
+def table_range(V, kmax, c_lo, c_hi, table="kappa", precision="fp64", out=None, workspace=None, check=True):
+    """The order-kmax entries of one table ("p0", "mu", "kappa", "spin_c",
+    "spin_kappa") whose largest mode lies in [c_lo, c_hi), in colex order
+    (gbs_table_range): a contiguous slice of the order-kmax group."""
+    V, M = _prep(V)
+    if table not in TABLES:
+        raise ValueError(f"table must be one of {sorted(TABLES)}")
+    if not (0 <= c_lo <= c_hi <= M):
+        raise ValueError(f"need 0 <= c_lo <= c_hi <= M = {M}")
+    n = range_entries(M, kmax, c_lo, c_hi)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.float64, device=V.device)
+    elif out.numel() < n or out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous CUDA float64 tensor of at least {n} entries")
+    _on(out, V.device, "out")
+    nb = int(lib().gbs_range_workspace_bytes(M, kmax, PRECISIONS[precision]))
+    if nb == 0:
+        raise GbsError(1, f"invalid (M={M}, kmax={kmax}, precision={precision})")
+    ws = _workspace_tensor(workspace, nb, V.device)
+    st = torch.cuda.current_stream(V.device)
+    _check(lib().gbs_table_range(_vp(V), M, kmax, TABLES[table], c_lo, c_hi, _vp(out), PRECISIONS[precision], _vp(ws),
+                                 _nbytes(ws), ctypes.c_void_p(st.cuda_stream)))
+    if check:
+        _check(lib().gbs_stream_status(_vp(ws), ctypes.c_void_p(st.cuda_stream)))
+    return out[:n]
+
+
 SAMPLE_PRECISIONS = {"fp64": 0, "fp32": 1}
 
 
@@ -316,7 +361,7 @@ def sample(kappa, M: int, K: int, u=None, force=None, orders=None, batch: int = 
                             None if q0 is None else _vp(q0), batch, SAMPLE_PRECISIONS[precision], _vp(ws),
                             _nbytes(ws), ctypes.c_void_p(st.cuda_stream)))
     if check:
-        torch.cuda.synchronize(dev)
+        _check(lib().gbs_stream_status(_vp(ws), ctypes.c_void_p(st.cuda_stream)))
     return bits, prob, q0
 
 

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <string>
 
 #include "gbs.h"
 #include "gbs_common.cuh"
@@ -38,13 +39,9 @@ int ok() {
     return GBS_OK;
 }
 
-// Orders 4 and 5 run the prefix-tree kernels (shared-memory x-entries sized for
-// GBS_MAX_MODES); orders 1-3 run one thread per subset and take larger M.
-int max_modes(int kmax) { return kmax <= 3 ? GBS_MAX_MODES_K3 : GBS_MAX_MODES; }
-
-bool valid_mk(int M, int kmax) {
-    return M >= 1 && kmax >= 1 && kmax <= GBS_MAX_ORDER && kmax <= M && M <= max_modes(kmax);
-}
+using gbs::valid_mk;
+static_assert(GBS_MAX_ORDER == 5 && GBS_MAX_MODES == 1024 && GBS_MAX_MODES_K3 == 4096,
+              "valid_mk (gbs_fwd.cuh) spells out the limits of gbs.h");
 
 int device_sms() {
     int dev = 0, sms = 0;
@@ -63,12 +60,16 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Workspace of a range call: the forward layout, then the lower orders of the
+// mode's table (the output slice holds only order kmax).
+size_t range_low_off(const gbs::WsLayout &L) { return L.total; }
+size_t range_total(const gbs::WsLayout &L, int M, int kmax) {
+    return L.total + ((sizeof(double) * (size_t)gbs::order_offset(M, kmax) + 255) & ~(size_t)255);
+}
+
 int check_common(const double *V, int M, int kmax, const void *out, int precision, void *ws, size_t ws_bytes,
-                 gbs::WsLayout &L, int &sms) {
-    if (!valid_mk(M, kmax))
-        return fail(GBS_ERR_INVALID_ARG,
-                    "need 1 <= kmax <= min(M, %d) and M <= %d (kmax >= 4) or %d (kmax <= 3); got M=%d kmax=%d",
-                    GBS_MAX_ORDER, GBS_MAX_MODES, GBS_MAX_MODES_K3, M, kmax);
+                 gbs::WsLayout &L, int &sms, bool range = false) {
+    if (!valid_mk(M, kmax)) return fail(GBS_ERR_INVALID_ARG, "%s", gbs::shape_message(M, kmax).c_str());
     if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
         return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 (0) or GBS_FP32_REFINED (1); got %d", precision);
     if (!V || !out || !ws) return fail(GBS_ERR_INVALID_ARG, "V, output and workspace must be non-NULL");
@@ -80,21 +81,33 @@ int check_common(const double *V, int M, int kmax, const void *out, int precisio
     sms = device_sms();
     if (sms <= 0) return fail(GBS_ERR_CUDA, "no CUDA device is current");
     L = gbs::ws_layout(M, kmax, sms);
-    if (ws_bytes < L.total)
-        return fail(GBS_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, L.total);
+    const size_t need = range ? range_total(L, M, kmax) : L.total;
+    if (ws_bytes < need)
+        return fail(GBS_ERR_WORKSPACE, "workspace too small: %zu bytes given, %zu needed", ws_bytes, need);
     return GBS_OK;
 }
 
+// Top-element range [c_lo, c_hi) of a range call; c_hi < 0 = whole tables.
+struct Range {
+    int c_lo = 0, c_hi = -1;
+    bool on() const { return c_hi >= 0; }
+};
+
 int run_forward(int mode, const double *V, int M, int kmax, double *out, int precision, void *ws, size_t ws_bytes,
-                void *stream, const double *mean = nullptr) {
+                void *stream, const double *mean = nullptr, Range range = Range{}) {
     gbs::WsLayout L;
     int sms = 0;
-    int rc = check_common(V, M, kmax, out, precision, ws, ws_bytes, L, sms);
+    if (range.on() && (range.c_lo < 0 || range.c_lo > range.c_hi || range.c_hi > M))
+        return fail(GBS_ERR_INVALID_ARG, "need 0 <= c_lo <= c_hi <= M; got c_lo=%d c_hi=%d M=%d", range.c_lo,
+                    range.c_hi, M);
+    int rc = check_common(V, M, kmax, out, precision, ws, ws_bytes, L, sms, range.on());
     if (rc != GBS_OK) return rc;
     if (mean && (((uintptr_t)mean & 7) || !is_device_ptr(mean)))
         return fail(GBS_ERR_INVALID_ARG, "mean must be 8-byte aligned CUDA device (or managed) memory");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *w = static_cast<char *>(ws);
+    if (gbs::fault_injected("forward_memset"))
+        return fail(GBS_ERR_CUDA, "cudaMemsetAsync: injected failure (GBS_FAULT_INJECT=forward_memset)");
     cudaError_t e = cudaMemsetAsync(w + L.status_off, 0, 256, st);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     gbs::FwdArgs a{};
@@ -107,8 +120,14 @@ int run_forward(int mode, const double *V, int M, int kmax, double *out, int pre
     a.A = reinterpret_cast<double *>(w + L.A_off);
     a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.p0f = reinterpret_cast<float *>(w + L.p0f_off);
-    a.p0 = (mode == gbs::MODE_P0) ? out : reinterpret_cast<double *>(w + L.p0_off);
-    a.out = out;
+    a.p0 = (mode == gbs::MODE_P0 && !range.on()) ? out : reinterpret_cast<double *>(w + L.p0_off);
+    a.out = range.on() ? reinterpret_cast<double *>(w + range_low_off(L)) : out;
+    if (range.on()) {
+        a.top = out;
+        a.top_base = gbs::order_offset(M, kmax) + gbs::binom(range.c_lo, kmax);
+        a.c_lo = range.c_lo;
+        a.c_hi = range.c_hi;
+    }
     a.status = reinterpret_cast<unsigned *>(w + L.status_off);
     a.counters = a.status + 8;
     a.scratch = reinterpret_cast<double *>(w + L.scratch_off);
@@ -141,6 +160,14 @@ namespace gbs {
 // Sets the message gbs_last_error() returns on this host thread; for entry
 // points defined in other translation units of the library.
 int record_error(int code, const char *msg) { return code == GBS_OK ? ok() : fail(code, "%s", msg); }
+
+std::string shape_message(int M, int kmax) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "need 1 <= kmax <= min(M, %d) and M <= %d (kmax >= 4) or %d (kmax <= 3); got M=%d kmax=%d",
+             GBS_MAX_ORDER, GBS_MAX_MODES, GBS_MAX_MODES_K3, M, kmax);
+    return buf;
+}
 }  // namespace gbs
 
 extern "C" {
@@ -472,6 +499,45 @@ int gbs_spin_correlators(const double *V, int M, int kmax, double *c_out, int pr
 int gbs_spin_cumulants(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
                        size_t ws_bytes, void *cuda_stream) {
     return run_forward(gbs::MODE_SPINK, V, M, kmax, kappa_out, precision, workspace, ws_bytes, cuda_stream);
+}
+
+size_t gbs_range_workspace_bytes(int M, int kmax, int precision) {
+    if (!valid_mk(M, kmax) || (precision != GBS_FP64 && precision != GBS_FP32_REFINED)) return 0;
+    const int sms = device_sms();
+    return range_total(gbs::ws_layout(M, kmax, sms > 0 ? sms : 1), M, kmax);
+}
+
+uint64_t gbs_range_entries(int M, int kmax, int c_lo, int c_hi) {
+    if (!valid_mk(M, kmax) || c_lo < 0 || c_lo > c_hi || c_hi > M) return 0;
+    return gbs::binom(c_hi, kmax) - gbs::binom(c_lo, kmax);
+}
+
+int gbs_range_split(int M, int kmax, int n_parts, int *bounds_out) {
+    if (!valid_mk(M, kmax)) return fail(GBS_ERR_INVALID_ARG, "%s", gbs::shape_message(M, kmax).c_str());
+    if (n_parts < 1 || n_parts > M || !bounds_out)
+        return fail(GBS_ERR_INVALID_ARG, "need 1 <= n_parts <= M and a host array of n_parts + 1 ints");
+    const uint64_t total = gbs::binom(M, kmax);
+    bounds_out[0] = 0;
+    int c = 0;
+    for (int i = 1; i < n_parts; ++i) {
+        // smallest c with C(c, kmax) >= i * total / n_parts (128-bit product: no overflow)
+        const uint64_t goal = (uint64_t)(((unsigned __int128)total * (unsigned)i) / (unsigned)n_parts);
+        while (c < M && gbs::binom(c, kmax) < goal) ++c;
+        bounds_out[i] = c;
+    }
+    bounds_out[n_parts] = M;
+    return ok();
+}
+
+int gbs_table_range(const double *V, int M, int kmax, int table, int c_lo, int c_hi, double *out, int precision,
+                    void *workspace, size_t ws_bytes, void *cuda_stream) {
+    if (table < GBS_TABLE_P0 || table > GBS_TABLE_SPIN_CUMULANT)
+        return fail(GBS_ERR_INVALID_ARG, "table must be one of the gbs_table values; got %d", table);
+    if (c_hi < 0) return fail(GBS_ERR_INVALID_ARG, "need 0 <= c_lo <= c_hi <= M; got c_hi=%d", c_hi);
+    Range r;
+    r.c_lo = c_lo;
+    r.c_hi = c_hi;
+    return run_forward(table, V, M, kmax, out, precision, workspace, ws_bytes, cuda_stream, nullptr, r);
 }
 
 int gbs_displaced_tables(const double *V, const double *mean, int M, int kmax, int table, double *out,

@@ -2,6 +2,8 @@
 // packed 2x2-block view of A = (V + I)/2, and 2x2 Cholesky/Schur steps in FP64.
 #pragma once
 #include <cstdint>
+#include <cstdlib>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace gbs {
@@ -186,6 +188,21 @@ __device__ __forceinline__ double quad_inv(const Sym &s, double idet, const Vec2
 
 __device__ __forceinline__ void flag_status(unsigned *status, unsigned bits) {
     if (status) atomicOr(status, bits);
+}
+
+// Host-side fault injection, for tests of the error paths: true when the
+// environment variable GBS_FAULT_INJECT lists `site` (comma-separated names).
+// Sites: "forward_memset" (the forward calls' first runtime call is treated as
+// failed, GBS_ERR_CUDA), "sampler_no_loads" (the sampler's tensor-core step
+// product issues no copies and gives up its first wait quickly, so the call
+// reports GBS_ERR_TIMEOUT with nothing in flight). Nothing faults on the GPU.
+inline bool fault_injected(const char *site) {
+    const char *env = getenv("GBS_FAULT_INJECT");
+    if (!env || !*env) return false;
+    const size_t n = strlen(site);
+    for (const char *p = env; (p = strstr(p, site)) != nullptr; p += n)
+        if ((p == env || p[-1] == ',') && (p[n] == '\0' || p[n] == ',')) return true;
+    return false;
 }
 
 }  // namespace gbs

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace gbs {
@@ -29,11 +30,26 @@ struct FwdArgs {
     int slots;            // number of slots = max persistent CTAs
     int sms;              // multiprocessors on the device
     cudaEvent_t *ev;      // GBS_MAX_ORDER + 2 timing events, or nullptr
+    // range call (gbs_table_range): order kmax is filled only for top elements in
+    // [c_lo, c_hi), into top[idx - top_base]; top = nullptr fills whole tables
+    double *top;
+    uint64_t top_base;
+    int c_lo, c_hi;
     // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
     // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
     // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area)
     int grain, ccap, variant;
 };
+
+// Valid (M, kmax) of a forward table: orders 4 and 5 run the prefix-tree kernels
+// (shared-memory x-entries sized for GBS_MAX_MODES); tables with kmax <= 3 run
+// one thread per subset and take up to GBS_MAX_MODES_K3 modes.
+inline bool valid_mk(int M, int kmax) {
+    return M >= 1 && kmax >= 1 && kmax <= 5 && kmax <= M && M <= (kmax <= 3 ? 4096 : 1024);
+}
+
+// Message for an (M, kmax) that valid_mk rejects (defined in gbs_api.cu).
+std::string shape_message(int M, int kmax);
 
 // Schedule of the prefix-tree kernels for one problem shape.
 struct TreeCfg {

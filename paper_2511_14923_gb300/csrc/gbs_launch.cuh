@@ -7,22 +7,24 @@
 
 namespace gbs {
 
+// Flat kernels of orders 1-3: one thread per subset of colex rank first + i,
+// i < count (the whole order, or the rank range of a range call's top order).
 template <int MODE, bool DISP>
-__global__ void order1_kernel(FwdArgs a, bool write_p0) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < a.M) order1_entry<MODE, DISP>(a, j, write_p0);
+__global__ void order1_kernel(FwdArgs a, bool write_p0, uint64_t first, uint64_t count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) order1_entry<MODE, DISP>(a, (int)(first + i), write_p0);
 }
 
 template <int MODE, bool DISP>
-__global__ void order2_kernel(FwdArgs a, bool write_p0) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < binom2(a.M)) order2_entry<MODE, DISP>(a, t, write_p0);
+__global__ void order2_kernel(FwdArgs a, bool write_p0, uint64_t first, uint64_t count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) order2_entry<MODE, DISP>(a, (uint32_t)(first + i), write_p0);
 }
 
 template <int MODE, bool DISP>
-__global__ void order3_kernel(FwdArgs a, bool write_p0) {
-    const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < binom(a.M, 3)) order3_entry<MODE, DISP>(a, r, write_p0);
+__global__ void order3_kernel(FwdArgs a, bool write_p0, uint64_t first, uint64_t count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) order3_entry<MODE, DISP>(a, first + i, write_p0);
 }
 
 template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
@@ -32,8 +34,11 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
     const int tid = threadIdx.x;
     const int M = a.M;
-    const int c4hi = c4_max<D>(M);
-    const int K = c4hi - 2;  // c4 runs c4hi, c4hi-1, .., 3
+    // top elements covered: all, or [c_lo, c_hi) for the top order of a range call
+    const bool ranged = a.top != nullptr && D == a.kmax;
+    const int tlo = ranged ? a.c_lo : 0, thi = ranged ? a.c_hi : M;
+    const int c4hi = c4_max<D>(M, thi);
+    const int K = c4hi - 2 > 0 ? c4hi - 2 : 0;  // c4 runs c4hi, c4hi-1, .., 3
     double *const slot = a.scratch + (size_t)blockIdx.x * a.slot_doubles;
 
     // prefix of item counts over c4 in descending order (warp 0, chunked scan)
@@ -41,7 +46,7 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
         const int per = (K + 31) / 32;
         const int lo = tid * per, hi = min(K, lo + per);
         uint32_t sum = 0;
-        for (int k = lo; k < hi; ++k) sum += items_for_c4<D>(M, c4hi - k, target);
+        for (int k = lo; k < hi; ++k) sum += items_for_c4<D>(M, c4hi - k, target, tlo, thi);
         uint32_t incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
         uint32_t run = incl - sum;
         for (int k = lo; k < hi; ++k) {
             sh.c4pref[k] = run;
-            run += items_for_c4<D>(M, c4hi - k, target);
+            run += items_for_c4<D>(M, c4hi - k, target, tlo, thi);
         }
         if (tid == 31) sh.c4pref[K] = incl;
     }
@@ -73,7 +78,7 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
         const int nc = n_classes(c4, target);
         const uint32_t rr = item - sh.c4pref[lo];
         const int u = (int)(rr / nc), s = (int)(rr % nc);
-        const int c5 = (D == 5) ? c4 + 1 + u : M;
+        const int c5 = (D == 5) ? c5_first(c4, tlo) + u : M;
         tree_item<D, MODE, PREC, NT, XC, DISP>(a, sh, slot, c4, c5, s, nc, write_p0, a.ccap);
     }
 }
@@ -83,7 +88,9 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
 template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
 static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
     const int M = a.M;
-    const uint64_t leaves = binom(M, D);
+    const bool ranged = a.top != nullptr && D == a.kmax;
+    const int tlo = ranged ? a.c_lo : 0, thi = ranged ? a.c_hi : M;
+    const uint64_t leaves = binom(thi, D) - binom(tlo, D);
     if (leaves == 0) return cudaSuccess;
     const size_t smem = sizeof(TreeShared<D, XC, DISP>);
     auto fn = tree_kernel<D, MODE, PREC, NT, XC, MINB, DISP>;
@@ -98,7 +105,7 @@ static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t s
     uint64_t target = leaves / ((uint64_t)grain * (uint64_t)grid_max);
     if (target < 256) target = 256;
     uint64_t items = 0;
-    for (int c4 = c4_max<D>(M); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, target);
+    for (int c4 = c4_max<D>(M, thi); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, target, tlo, thi);
     if (items == 0) return cudaSuccess;
     const int grid = (int)(items < (uint64_t)grid_max ? items : (uint64_t)grid_max);
     fn<<<grid, NT, smem, st>>>(a, target, write_p0);
@@ -135,19 +142,33 @@ static cudaError_t launch_mode(const FwdArgs &a, cudaStream_t st) {
     auto mark = [&](int i) {
         if (a.ev) cudaEventRecord(a.ev[i], st);
     };
+    // ranks of order d to fill: all, or those with top element in [c_lo, c_hi)
+    // for the top order of a range call
+    auto span = [&](int d, uint64_t &first, uint64_t &count) {
+        if (a.top && d == a.kmax) {
+            first = binom(a.c_lo, d);
+            count = binom(a.c_hi, d) - first;
+        } else {
+            first = 0;
+            count = binom(M, d);
+        }
+    };
+    auto grid = [](uint64_t n) { return (unsigned)((n + FLAT_THREADS - 1) / FLAT_THREADS); };
     cudaError_t e = cudaSuccess;
-    order1_kernel<MODE, DISP><<<(M + FLAT_THREADS - 1) / FLAT_THREADS, FLAT_THREADS, 0, st>>>(a, wp(1));
+    uint64_t f = 0, n = 0;
+    span(1, f, n);
+    if (n) order1_kernel<MODE, DISP><<<grid(n), FLAT_THREADS, 0, st>>>(a, wp(1), f, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     mark(2);
     if (a.kmax >= 2) {
-        const uint64_t n2 = binom2(M);
-        order2_kernel<MODE, DISP><<<(unsigned)((n2 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(2));
+        span(2, f, n);
+        if (n) order2_kernel<MODE, DISP><<<grid(n), FLAT_THREADS, 0, st>>>(a, wp(2), f, n);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     mark(3);
     if (a.kmax >= 3) {
-        const uint64_t n3 = binom(M, 3);
-        order3_kernel<MODE, DISP><<<(unsigned)((n3 + FLAT_THREADS - 1) / FLAT_THREADS), FLAT_THREADS, 0, st>>>(a, wp(3));
+        span(3, f, n);
+        if (n) order3_kernel<MODE, DISP><<<grid(n), FLAT_THREADS, 0, st>>>(a, wp(3), f, n);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     mark(4);

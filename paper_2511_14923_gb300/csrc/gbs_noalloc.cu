@@ -67,8 +67,7 @@ bool on_device(const void *p) {
 }  // namespace
 
 extern "C" int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *kappa_out, void *cuda_stream) {
-    if (M < 1 || M > GBS_MAX_MODES || kmax < 1 || kmax > GBS_MAX_ORDER || kmax > M)
-        return gbs::record_error(GBS_ERR_INVALID_ARG, "need 1 <= M <= 1024 and 1 <= kmax <= min(M, 5)");
+    if (!gbs::valid_mk(M, kmax)) return gbs::record_error(GBS_ERR_INVALID_ARG, gbs::shape_message(M, kmax).c_str());
     if (!V || !kappa_out) return gbs::record_error(GBS_ERR_INVALID_ARG, "V and kappa_out must be non-NULL");
     if (((uintptr_t)V & 7) || ((uintptr_t)kappa_out & 7))
         return gbs::record_error(GBS_ERR_INVALID_ARG, "V and kappa_out must be 8-byte aligned");
@@ -122,4 +121,12 @@ extern "C" int gbs_cumulants_noalloc(const double *V, int M, int kmax, double *k
         return gbs::record_error(GBS_ERR_CUDA, msg);
     }
     return gbs::record_error(GBS_OK, "");
+}
+
+extern "C" int gbs_noalloc_status(void *cuda_stream) {
+    void *ws = nullptr;
+    const int rc = scratch_address(&ws);
+    if (rc != GBS_OK) return rc;
+    // the status word sits at the start of the scratch array (workspace layout offset 0)
+    return gbs_stream_status(ws, cuda_stream);
 }

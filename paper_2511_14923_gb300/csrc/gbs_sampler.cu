@@ -93,6 +93,8 @@ struct Args {
     const double *H;       // per-variable log scale ln s_v (the click entropy of mode v - 1)
     unsigned *status;      // status word (ST_* bits), first bytes of the workspace
     int use_tc;            // FP32: step product on the tensor cores
+    int wait_limit;        // polls of an mbarrier before a wait gives up (ST_TIMEOUT)
+    int no_loads;          // test hook: the step product issues no copies (its first wait runs out)
     uint32_t *bw;          // spins as bits: word w of sample s at bw[w * S + s], bit v & 31 = x_v
     const double *u;       // [n_samples][M] uniforms (chunk base)
     const uint8_t *force;  // [n_samples][M] or null
@@ -403,9 +405,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
 
-// Bounded wait for phase `parity` of the mbarrier; false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
+// Bounded wait for phase `parity` of the mbarrier: at most `limit` polls
+// (try_wait may itself suspend the thread briefly); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -582,15 +585,27 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
             tma_bulk(sp, Ab + (size_t)c * 2 * 4096, 2 * TC_AB, &full[c & 1]);
             tma_bulk(sp + 2 * TC_AB, Wb + (size_t)c * nsb * 2 * 8192, 2 * TC_BB, &full[c & 1]);
         };
-        uint32_t ph_full[2] = {0u, 0u}, ph_empty[2] = {0u, 0u};
+        // chunk c uses stage c & 1 and completes phase (c >> 1) & 1 of its barriers;
+        // nl chunks loaded, nf of them waited for (full), nc committed, ne of those
+        // waited for (empty)
+        int nl = 0, nf = 0, nc = 0, ne = 0;
+        const int lim = a.wait_limit;
+        auto wait_full = [&](int c) { return mbar_wait(&full[c & 1], (uint32_t)(c >> 1) & 1u, lim); };
+        auto wait_empty = [&](int c) { return mbar_wait(&empty[c & 1], (uint32_t)(c >> 1) & 1u, lim); };
         bool ok = true;
-        load(0);
-        if (nk > 1) load(1);
+        if (!a.no_loads) {
+            load(0);
+            ++nl;
+            if (nk > 1) {
+                load(1);
+                ++nl;
+            }
+        }
         for (int c = 0; c < nk && ok; ++c) {
             const int st = c & 1;
-            ok = mbar_wait(&full[st], ph_full[st]);
-            ph_full[st] ^= 1u;
+            ok = wait_full(c);
             if (!ok) break;
+            ++nf;
             tc_fence_after();
             const uint32_t sbs = sbase + st * TC_STAGE;
 #pragma unroll
@@ -603,23 +618,30 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
                 tc_mma(tmem, alo, bhi, 1u);
             }
             tc_commit(&empty[st]);
+            ++nc;
             // refill the other stage with chunk c+1 once the MMAs of chunk c-1 are done
             if (c >= 1 && c + 1 < nk) {
-                const int so = (c + 1) & 1;
-                ok = mbar_wait(&empty[so], ph_empty[so]);
-                ph_empty[so] ^= 1u;
-                if (ok) load(c + 1);
+                ok = wait_empty(c - 1);
+                if (ok) {
+                    ++ne;
+                    load(c + 1);
+                    ++nl;
+                }
             }
         }
         // the loop waited for chunks 0 .. nk-3; wait for the last two
-        for (int c = (nk >= 2 ? nk - 2 : 0); c < nk && ok; ++c) {
-            const int st = c & 1;
-            ok = mbar_wait(&empty[st], ph_empty[st]);
-            ph_empty[st] ^= 1u;
+        while (ok && ne < nc) {
+            ok = wait_empty(ne);
+            if (ok) ++ne;
         }
         if (!ok) {
             *flag = 0;
             if (a.status) atomicOr(a.status, ST_TIMEOUT);
+            // drain what this thread issued before leaving: copies not yet waited
+            // for, then committed MMAs, each wait bounded again; what is still
+            // outstanding after that is abandoned (the kernel has already failed)
+            for (int c = nf; c < nl; ++c) wait_full(c);
+            for (int c = ne; c < nc; ++c) wait_empty(c);
         }
     }
     tc_fence_before();
@@ -1423,6 +1445,12 @@ static cudaError_t run_all(const SamplerCall &c, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     a.use_tc = 0;
+    a.wait_limit = 1 << 22;
+    a.no_loads = 0;
+    if (fault_injected("sampler_no_loads")) {
+        a.no_loads = 1;
+        a.wait_limit = 1 << 10;
+    }
     if (sizeof(R) == 4) {
         const char *env = getenv("GBS_SAMPLER_SIMT");
         a.use_tc = (env && *env && *env != '0') || c.S % TC_N != 0 ? 0 : 1;

@@ -129,6 +129,9 @@ __device__ __forceinline__ double combine_tail(double acc, int j, int c2, uint32
     return acc;
 }
 
+template <int MODE>
+__device__ __forceinline__ void store_entry(const FwdArgs &a, int d, uint64_t idx, double P0, double v, bool write_p0);
+
 // ---------------------------------------------------------------- small kernels
 
 // Writes block idx = x*M + y of A = (V+I)/2 as 4 doubles, and (if Af is not
@@ -169,11 +172,11 @@ __device__ __forceinline__ void order1_entry(const FwdArgs &a, int j, bool write
         flag_status(a.status, ST_NOT_POSDEF);
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
     }
-    if (write_p0) a.p0[j] = P0;
     if (a.p0f && a.precision == 1) split_df(P0, a.p0f[2 * j], a.p0f[2 * j + 1]);
     // mu({j}) = kt({j}) = 1 - P0({j});  c({j}) = kappa({j}) = 2 P0({j}) - 1
-    if (MODE == MODE_MU || MODE == MODE_KAPPA) a.out[j] = 1.0 - P0;
-    if (MODE == MODE_SPINC || MODE == MODE_SPINK) a.out[j] = fma(2.0, P0, -1.0);
+    const double v = (MODE == MODE_MU || MODE == MODE_KAPPA) ? 1.0 - P0
+                   : (MODE == MODE_SPINC || MODE == MODE_SPINK) ? fma(2.0, P0, -1.0) : P0;
+    store_entry<MODE>(a, 1, (uint64_t)j, P0, v, write_p0);
 }
 
 
@@ -199,12 +202,13 @@ __device__ __forceinline__ void order2_entry(const FwdArgs &a, uint32_t t, bool 
         P0 = __longlong_as_double(0x7ff8000000000000ULL);
     }
     const uint64_t idx = (uint64_t)M + t;
-    if (write_p0) a.p0[idx] = P0;
-    if (MODE == MODE_MU) a.out[idx] = a.out[c2] - a.p0[j] + P0;
-    if (MODE == MODE_KAPPA) a.out[idx] = fma(-a.p0[j], a.p0[c2], P0);
+    double v = P0;
+    if (MODE == MODE_MU) v = a.out[c2] - a.p0[j] + P0;
+    if (MODE == MODE_KAPPA) v = fma(-a.p0[j], a.p0[c2], P0);
     // c({j,c2}) = -c({c2}) - 2 (P0({j}) - 2 P0(S));  kappa(S) = 4 (P0(S) - P0({j}) P0({c2}))
-    if (MODE == MODE_SPINC) a.out[idx] = fma(4.0, P0, fma(-2.0, a.p0[j], -a.out[c2]));
-    if (MODE == MODE_SPINK) a.out[idx] = 4.0 * fma(-a.p0[j], a.p0[c2], P0);
+    if (MODE == MODE_SPINC) v = fma(4.0, P0, fma(-2.0, a.p0[j], -a.out[c2]));
+    if (MODE == MODE_SPINK) v = 4.0 * fma(-a.p0[j], a.p0[c2], P0);
+    store_entry<MODE>(a, 2, idx, P0, v, write_p0);
 }
 
 
@@ -243,9 +247,7 @@ __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool 
     }
     const double p0R[2] = {0.0, a.p0[idxQ[1]]};
     const double v = combine<1, MODE>(P0, j, c2, t, baseJ, baseT, p0R, a.p0, a.out);
-    const uint64_t idx = baseT[1] + t;
-    if (write_p0) a.p0[idx] = P0;
-    if (MODE != MODE_P0) a.out[idx] = v;
+    store_entry<MODE>(a, 3, baseT[1] + t, P0, v, write_p0);
 }
 
 
@@ -343,15 +345,47 @@ __host__ __device__ __forceinline__ int n_classes(int c4, uint64_t target) {
     return (int)n;
 }
 
+// Items of the order-D prefix tree whose top element (c5 for D = 5, c4 for
+// D = 4) lies in [lo, hi): the largest c4 that has any, and the items of one c4.
+template <int D>
+__host__ __device__ __forceinline__ int c4_max(int M, int hi) {
+    const int top = hi < M ? hi : M;
+    return D == 5 ? top - 2 : top - 1;
+}
 template <int D>
 __host__ __device__ __forceinline__ int c4_max(int M) {
-    return D == 5 ? M - 2 : M - 1;
+    return c4_max<D>(M, M);
 }
 
+// First top element c5 of the items of one c4 (D = 5).
+__host__ __device__ __forceinline__ int c5_first(int c4, int lo) { return c4 + 1 > lo ? c4 + 1 : lo; }
+
+template <int D>
+__host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_t target, int lo, int hi) {
+    int nU;
+    if (D == 5) {
+        const int first = c5_first(c4, lo), last = hi < M ? hi : M;
+        nU = last > first ? last - first : 0;
+    } else {
+        nU = (c4 >= lo && c4 < hi) ? 1 : 0;
+    }
+    return (uint32_t)nU * (uint32_t)n_classes(c4, target);
+}
 template <int D>
 __host__ __device__ __forceinline__ uint32_t items_for_c4(int M, int c4, uint64_t target) {
-    const uint32_t nU = D == 5 ? (uint32_t)(M - 1 - c4) : 1u;
-    return nU * (uint32_t)n_classes(c4, target);
+    return items_for_c4<D>(M, c4, target, 0, M);
+}
+
+// Stores entry idx (table layout) of order d: into the caller's slice of order
+// kmax during a range call, else into the P0 table (write_p0) and the mode's table.
+template <int MODE>
+__device__ __forceinline__ void store_entry(const FwdArgs &a, int d, uint64_t idx, double P0, double v, bool write_p0) {
+    if (a.top && d == a.kmax) {
+        a.top[idx - a.top_base] = (MODE == MODE_P0) ? P0 : v;
+        return;
+    }
+    if (write_p0) a.p0[idx] = P0;
+    if (MODE != MODE_P0) a.out[idx] = v;
 }
 
 // One work item of the prefix-tree kernel: U = {c4, c5} (D = 5) or {c4} (D = 4),
@@ -677,7 +711,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                                 flag_status(a.status, ST_NOT_POSDEF);
                                 v = __longlong_as_double(0x7ff8000000000000ULL);
                             }
-                            a.out[bT[PALL] + t] = v;
+                            store_entry<MODE>(a, NP + 2, bT[PALL] + t, 0.0, v, false);
                             continue;
                         }
                     }
@@ -688,9 +722,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                     P0 = __longlong_as_double(0x7ff8000000000000ULL);
                 }
                 const double v = combine<NP, MODE>(P0, j, c2, t, bJ, bT, sh.p0R[b], a.p0, a.out);
-                const uint64_t idx = bT[PALL] + t;
-                if (write_p0) a.p0[idx] = P0;
-                if (MODE != MODE_P0) a.out[idx] = v;
+                store_entry<MODE>(a, NP + 2, bT[PALL] + t, P0, v, write_p0);
             }
         }
         __syncthreads();

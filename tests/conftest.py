@@ -10,6 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "full: full-size oracle comparison (opt-in, GBS_FULL_PARITY=1)")
 
 
 def pytest_collection_modifyitems(config, items):

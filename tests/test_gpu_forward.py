@@ -166,3 +166,17 @@ def test_refined_path_differs_from_fp64_only_by_rounding():
     n3 = gbs.table_size(40, 3)
     assert np.any(a[n3:] != b[n3:])
     assert np.abs(b / a - 1).max() <= 1e-11
+
+
+def test_injected_runtime_failure_is_reported(monkeypatch):
+    """A runtime-call failure inside the library (injected on the host) comes
+    back as GBS_ERR_CUDA with a message; the next call succeeds."""
+    inst = synthetic.config(0)
+    V = torch.from_numpy(inst.V).cuda()
+    monkeypatch.setenv("GBS_FAULT_INJECT", "forward_memset")
+    with pytest.raises(gbs.GbsError) as err:
+        gbs.cumulants(V, inst.kmax)
+    assert err.value.code == 3 and "injected" in str(err.value)
+    monkeypatch.delenv("GBS_FAULT_INJECT")
+    kt = gbs.cumulants(V, inst.kmax).cpu().numpy()
+    assert np.abs(kt - oracle.tables(inst.V, inst.kmax)[2]).max() <= 1e-12

@@ -148,3 +148,22 @@ def test_fp32_tensor_core_product_matches_simt(monkeypatch):
     assert float(same.float().mean()) > 0.9
     assert torch.abs(l_tc[same] - l_s[same]).max().item() <= 1e-3
     assert torch.abs(q_tc[same] - q_s[same]).max().item() <= 2e-4
+
+
+def test_status_word_read_after_a_call(monkeypatch):
+    """check=True reads the status word the sampler keeps in its workspace: GBS_OK
+    after a normal call; GBS_ERR_TIMEOUT when the tensor-core step product's
+    first wait runs out (host-side injection: the product issues no copies, so
+    nothing is in flight when it gives up); afterwards the context is intact and
+    a normal call reproduces the first call's bits."""
+    inst = synthetic.random_instance(24, 5, seed=44)
+    kap = kappa_of(inst, 5)
+    u = torch.from_numpy(uniforms(256, 24, 9)).cuda()
+    bits, logp, _ = gbs.sample(kap, 24, 5, u=u, batch=256, precision="fp32", check=True)
+    monkeypatch.setenv("GBS_FAULT_INJECT", "sampler_no_loads")
+    with pytest.raises(gbs.GbsError) as err:
+        gbs.sample(kap, 24, 5, u=u, batch=256, precision="fp32", check=True)
+    assert err.value.code == 4
+    monkeypatch.delenv("GBS_FAULT_INJECT")
+    bits2, logp2, _ = gbs.sample(kap, 24, 5, u=u, batch=256, precision="fp32", check=True)
+    assert torch.equal(bits, bits2) and torch.equal(logp, logp2)

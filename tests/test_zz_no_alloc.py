@@ -59,3 +59,33 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rc = f(ctypes.c_void_p(V.data_ptr()), 144, 5, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == 5
     assert b"allocation-free" in gbs.lib().gbs_last_error()
+
+
+def test_noalloc_shape_check_matches_the_workspace_entry():
+    """kmax <= 3 tables take up to 4096 modes: a valid shape too large for the fixed
+    array is a workspace error, as documented, not an argument error."""
+    f = noalloc_fn()
+    M = 2048
+    V = torch.eye(2 * M, dtype=torch.float64, device="cuda")
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    assert f(ctypes.c_void_p(V.data_ptr()), M, 3, ctypes.c_void_p(out.data_ptr()), None) == 5
+    assert f(ctypes.c_void_p(V.data_ptr()), M, 4, ctypes.c_void_p(out.data_ptr()), None) == 1
+
+
+def test_noalloc_status_is_queryable():
+    """gbs_noalloc_status reports the device status of the allocation-free calls,
+    whose callers hold no workspace to pass to gbs_stream_status."""
+    f = noalloc_fn()
+    q = gbs.lib().gbs_noalloc_status
+    q.argtypes = [ctypes.c_void_p]
+    q.restype = ctypes.c_int
+    inst = synthetic.random_instance(20, 4, seed=303)
+    V = torch.from_numpy(inst.V).cuda()
+    call_noalloc(f, V, 20, 4)
+    assert q(None) == 0
+    bad = V.clone()
+    bad[3, 3] = -5.0  # (V_T + I)/2 not positive definite for every T holding mode 3
+    out = call_noalloc(f, bad, 20, 4)
+    assert q(None) == 2 and torch.isnan(out).any()
+    call_noalloc(f, V, 20, 4)
+    assert q(None) == 0
