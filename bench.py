@@ -410,7 +410,7 @@ def run_batch(precision, steps, warmup, autotune, peaks, sms, sm_mhz):
 # counters of one gbs_cumulants_backward call (sum over the phase's kernels);
 # None = not captured.
 FIT_PHASE_FP64_FLOPS = {"p0_recompute": 235197625, "h_table": 2293700, "gp0_gather": 194452675,
-                        "gv_scatter": 2029657521}
+                        "gv_scatter": 1417270000}
 
 
 def run_fit(steps, warmup, peaks):
@@ -427,6 +427,8 @@ def run_fit(steps, warmup, peaks):
     w = gbs.fit_weights(M, K, device="cuda")
     r = torch.from_numpy(inst.r).cuda().requires_grad_(True)
     eta = torch.from_numpy(inst.eta).cuda().requires_grad_(True)
+    # untimed: the prefix-tree schedule for this shape (forward and the adjoint's P0 pass)
+    gbs.autotune(gbs.covariance(U, r.detach(), eta.detach()), K, "fp64")
 
     def step():
         V = gbs.CovarianceFn.apply(r, eta, U)
@@ -461,7 +463,7 @@ def run_fit(steps, warmup, peaks):
     if FIT_PHASE_FP64_FLOPS:
         roof["fp64"] = {k: {"achieved_tflops": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / 1e12,
                             "frac": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / peaks["fp64_flops"]}
-                        for k, t in zip(names, phases) if k in FIT_PHASE_FP64_FLOPS and t > 0}
+                        for k, t in zip(names, phases) if FIT_PHASE_FP64_FLOPS.get(k) and t > 0}
     N = gbs.table_size(M, K)
     return {"metric": "fitting step (forward + adjoint), M=100 kmax=4", "value": N / (ms * 1e-3),
             "unit": "subsets/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,

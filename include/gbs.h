@@ -280,7 +280,8 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
    schedule of the prefix-tree kernels -- items per CTA (1, 2, 4, 8), children
    per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, 256 x 2
    per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, 256 x 3 when
-   M <= 577, and 768 x 1 with a larger shared-memory batch area) -- and records
+   M <= 577, 768 x 1 with a larger shared-memory batch area, 384 x 2 when
+   M <= 961, and 256 x 4 when M <= 385) -- and records
    the fastest in a process-wide table that
    later forward calls of that shape use. If the environment variable
    GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and
@@ -337,7 +338,8 @@ int gbs_cumulants_batched(int precision, void *workspace, void *cuda_stream);
 /* Batch autotuner (the schedule search of gbs_autotune, for a ragged batch):
    times gbs_cumulants_batched on this batch under candidate schedules -- every
    CTA shape allowed for the precision and the largest M (512 x 1, 256 x 2 when
-   M <= 577; refined also 640 x 1, 256 x 3 when M <= 577, and 768 x 1) at the default
+   M <= 577; refined also 640 x 1, 256 x 3 when M <= 577, 768 x 1, 384 x 2
+   when M <= 961, and 256 x 4 when M <= 385) at the default
    grain and batch size, then items per CTA slot (1, 2, 4, 8) x children per
    batch (16, 64) for the fastest shape -- records the fastest for this batch
    shape (multiset of (M, kmax), device, precision; persisted like gbs_autotune's
@@ -352,7 +354,8 @@ int gbs_batched_autotune(const gbs_instance *inst, int n, int precision, void *w
    gbs_batched_autotune in this process): schedule_out[5] (host) = {CTA shape
    (0: 512 threads x 1 per SM, 1: 256 x 2, 2: 640 x 1, 3: 256 x 3), threads per
    CTA, CTAs in the launch, items per CTA slot, children per shared-memory
-   batch}, shape 4 being 768 threads x 1. Returns GBS_OK or GBS_ERR_INVALID_ARG
+   batch}, shape 4 being 768 threads x 1, 5 384 x 2 and 6 256 x 4. Returns GBS_OK or
+   GBS_ERR_INVALID_ARG
    (no plan). */
 int gbs_batched_schedule(const void *workspace, int *schedule_out);
 

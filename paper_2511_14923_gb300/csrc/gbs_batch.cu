@@ -36,9 +36,6 @@ namespace {
 
 constexpr int NPHASE = 6;
 constexpr unsigned PLAN_MAGIC = 0x67627332u;
-// Scratch slots reserved per multiprocessor: enough for the CTA shape with the
-// most resident CTAs (256 threads x 3), so any schedule fits one workspace.
-constexpr int kSlotsPerSm = 3;
 
 struct InstDev {
     const double *V;
@@ -83,7 +80,8 @@ int max_m(const gbs_instance *in, int n) {
 
 // Builds the plan for a schedule (grain, ccap) and a launch of grid CTAs of the
 // shape (nt, xc); pointers inside InstDev are relative to base (nullptr base =
-// sizes only). The scratch area always holds kSlotsPerSm slots per multiprocessor.
+// sizes only). The scratch area holds slots_per_sm_for(maxM) slots per
+// multiprocessor, enough for every CTA shape the batch allows.
 void build_plan(const gbs_instance *in, int n, int precision, int sms, int grid, int nt, int xc, int grain, int ccap,
                 char *base, HostPlan &hp) {
     std::vector<int> order(n);
@@ -163,7 +161,7 @@ void build_plan(const gbs_instance *in, int n, int precision, int sms, int grid,
     }
     for (int ph = 0; ph < NPHASE; ++ph) hp.hdr.total[ph] = hp.pref[(size_t)ph * (n + 1) + n];
     hp.scratch_off = off;
-    off = a256(off + sizeof(double) * hp.hdr.slot_doubles * (size_t)kSlotsPerSm * (size_t)(sms > 0 ? sms : 1));
+    off = a256(off + sizeof(double) * hp.hdr.slot_doubles * (size_t)slots_per_sm_for(maxM) * (size_t)(sms > 0 ? sms : 1));
     hp.total = off;
 }
 
@@ -254,7 +252,7 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(char *ws) {
     // a plan made for another kernel or grid is refused before any barrier (the
     // test is uniform across the grid, so every CTA returns)
     if (h.magic != PLAN_MAGIC || h.precision != PREC || h.nt != NT || h.xc != XC || h.grid != (int)gridDim.x ||
-        h.maxM > (XC < GBS_MAX_MODES ? kVariant1MaxM : GBS_MAX_MODES) || h.ccap < 1 || h.ccap > CCAP) {
+        h.maxM > (XC < GBS_MAX_MODES ? XC + 1 : GBS_MAX_MODES) || h.ccap < 1 || h.ccap > CCAP) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(status, ST_BAD_INDEX);
         return;
     }
@@ -301,7 +299,8 @@ __global__ void __launch_bounds__(NT, MINB) batched_kernel(char *ws) {
 
 // Kernel of one CTA shape (variant numbering as for the single-instance
 // schedules: 0 = 512 x 1, 1 = 256 x 2, refined only 2 = 640 x 1, 3 = 256 x 3,
-// 4 = 768 x 1 with a 2048-entry x area).
+// 4 = 768 x 1 with a 2048-entry x area, 5 = 384 x 2 with a 960-entry x area,
+// 6 = 256 x 4 with a 384-entry x area).
 struct KernelInfo {
     void *fn;
     int nt, xc;
@@ -317,6 +316,8 @@ bool variant_ok(int precision, int variant, int maxM) {
     if (variant < 0 || variant >= kNumVariants) return false;
     if (precision == 0 && variant >= 2) return false;
     if ((variant == 1 || variant == 3) && maxM > kVariant1MaxM) return false;
+    if (variant == 5 && maxM > kVariant5MaxM) return false;
+    if (variant == 6 && maxM > kVariant6MaxM) return false;
     return true;
 }
 
@@ -327,19 +328,21 @@ KernelInfo kernel_for(int precision, int variant) {
         case 2: return kinfo<1, 640, XCAP, 1>();
         case 3: return kinfo<1, 256, 576, 3>();
         case 4: return kinfo<1, 768, kWideXC, 1>();
+        case 5: return kinfo<1, 384, kPairXC, 2>();
+        case 6: return kinfo<1, 256, kQuadXC, 4>();
         default: return kinfo<1, TREE_THREADS, XCAP, 1>();
     }
 }
 
 // Co-resident CTAs of a shape on this device (cooperative launch), at most
-// kSlotsPerSm per multiprocessor.
-cudaError_t grid_for(const KernelInfo &k, int sms, int &grid) {
+// slots_per_sm per multiprocessor.
+cudaError_t grid_for(const KernelInfo &k, int sms, int slots_per_sm, int &grid) {
     cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.nt, k.smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    grid = sms * std::min(per_sm, kSlotsPerSm);
+    grid = sms * std::min(per_sm, slots_per_sm);
     return cudaSuccess;
 }
 
@@ -364,7 +367,7 @@ int write_plan(const gbs_instance *inst, int n, int precision, char *ws, size_t 
                cudaStream_t st, size_t &needed) {
     const KernelInfo k = kernel_for(precision, cfg.variant);
     int grid = 0;
-    if (grid_for(k, sms, grid) != cudaSuccess) return GBS_ERR_CUDA;
+    if (grid_for(k, sms, slots_per_sm_for(max_m(inst, n)), grid) != cudaSuccess) return GBS_ERR_CUDA;
     HostPlan hp;
     build_plan(inst, n, precision, sms, grid, k.nt, k.xc, cfg.grain, cfg.ccap, ws, hp);
     needed = hp.total;
@@ -390,7 +393,8 @@ int write_plan(const gbs_instance *inst, int n, int precision, char *ws, size_t 
 
 size_t batched_workspace_bytes(const gbs_instance *inst, int n, int precision, int sms) {
     HostPlan hp;
-    build_plan(inst, n, precision, sms, sms * kSlotsPerSm, TREE_THREADS, XCAP, kDefaultCfg.grain, kDefaultCfg.ccap,
+    build_plan(inst, n, precision, sms, sms * slots_per_sm_for(max_m(inst, n)), TREE_THREADS, XCAP, kDefaultCfg.grain,
+               kDefaultCfg.ccap,
                nullptr, hp);
     return hp.total;
 }

@@ -304,29 +304,68 @@ __global__ void ainv_kernel(int M, const double *__restrict__ A, double *__restr
         }
 }
 
-// dL/dV for the order-D subsets T = {j} + T' (j < min T'), one warp per T'
-// (order DP = D - 1), lanes over j. With A' = A_{T'}, b = A[T', j], a = A_jj,
-// u = A'^{-1} b, S = a - b^T u (the Schur complement) and v = u S^{-1}:
+// dL/dV for the order-D subsets T = {j} + T' (j < s0 = min T'), one thread per
+// prefix T' (order DP = D - 1) looping over its s0 leaves. With A' = A_{T'},
+// b = A[T', j], a = A_jj, u = A'^{-1} b, S = a - b^T u (the Schur complement)
+// and v = u S^{-1}:
 //   A_T^{-1} = [[A'^{-1} + v u^T, -v], [-v^T, S^{-1}]].
-// The T' x T' block is summed over the warp's leaves and added once; the j rows
-// go straight to dV. Each contribution is C(T) A_T^{-1}, C(T) = -1/4 gP0(T) P0(T).
-template <int DP>
-__global__ void __launch_bounds__(256, 2) gv2_kernel(int M, Offsets o, const double *__restrict__ A,
-                                                     const double *__restrict__ p0, const double *__restrict__ gp0,
-                                                     const double *__restrict__ inv, double *__restrict__ gV,
-                                                     unsigned *status) {
+// Each contribution is C(T) A_T^{-1}, C(T) = -1/4 gP0(T) P0(T). The thread keeps
+// A'^{-1} and the T' x T' block's running sum (sum_j C) A'^{-1} + sum_j C v u^T
+// in registers and adds the block once; the j rows go straight to dV.
+// With L = 0 a thread takes all leaves of its prefix. Prefixes are then
+// numbered by their smallest element s0 (the C(M-1-s0, DP-1) of them with
+// smallest element s0 follow the C(M-1, DP) - C(M-s0, DP) with a smaller one,
+// s0 >= 1), so the threads of a warp share s0 and the trip count; the largest s0
+// come first (thread gi takes prefix n - 1 - gi). With L > 0 (the low orders,
+// whose few prefixes would leave most of the GPU idle), thread x of grid row y
+// takes leaves [y L, y L + L) of the prefix of colex rank x, and adds its part of
+// the T' x T' block on its own.
+template <int DP, int L>
+__global__ void __launch_bounds__(128) gv2_kernel(int M, Offsets o, const double *__restrict__ A,
+                                                  const double *__restrict__ p0, const double *__restrict__ gp0,
+                                                  const double *__restrict__ inv, double *__restrict__ gV,
+                                                  unsigned *status) {
     constexpr int N = 2 * DP, NT = N * (N + 1) / 2, D = DP + 1;
-    __shared__ double sai[8][NT];  // the warp's A_{T'}^{-1} (blockDim 256 = 8 warps)
-    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    if (w >= binom(M, DP)) return;  // whole warps leave together; no block barrier below
     int s[DP];
-    colex_unrank(w, DP, s);
+    int j0, j1;
+    if constexpr (L == 0) {
+        const uint64_t nthr = binom(M - 1, DP);
+        const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (gi >= nthr) return;
+        const uint64_t i = nthr - 1 - gi;
+        // s0: the last s in [1, M - DP] with C(M-1, DP) - C(M-s, DP) <= i
+        int lo = 1, hi = M - DP + 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (nthr - binom(M - mid, DP) <= i) lo = mid;
+            else hi = mid;
+        }
+        s[0] = lo;
+        if constexpr (DP > 1) {
+            int e[DP - 1];
+            colex_unrank(i - (nthr - binom(M - lo, DP)), DP - 1, e);
+#pragma unroll
+            for (int k = 0; k < DP - 1; ++k) s[k + 1] = lo + 1 + e[k];
+        }
+        j0 = 0;
+        j1 = s[0];
+    } else {
+        const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (w >= binom(M, DP)) return;
+        colex_unrank(w, DP, s);
+        j0 = (int)blockIdx.y * L;
+        j1 = j0 + L < s[0] ? j0 + L : s[0];
+        if (j0 >= j1) return;
+    }
+    const int s0 = s[0];
     const int n2 = 2 * M;
-    const double *Ai = inv + (size_t)w * NT;
-    double *ai = sai[wib];
-    for (int q = lane; q < NT; q += 32) ai[q] = Ai[q];
-    __syncwarp();
+    // A'^{-1} (packed lower triangle) of T', whose colex rank among the order-DP subsets is w
+    uint64_t w = 0;
+#pragma unroll
+    for (int u = 0; u < DP; ++u) w += binom(s[u], u + 1);
+    double ai[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) ai[q] = inv[w * NT + q];
     auto AI = [&](int r, int c) { return r >= c ? ai[r * (r + 1) / 2 + c] : ai[c * (c + 1) / 2 + r]; };
     int gr[N];
 #pragma unroll
@@ -338,7 +377,8 @@ __global__ void __launch_bounds__(256, 2) gv2_kernel(int M, Offsets o, const dou
     double sumC = 0.0, acc[NT];
 #pragma unroll
     for (int q = 0; q < NT; ++q) acc[q] = 0.0;
-    for (int j = lane; j < s[0]; j += 32) {
+    (void)s0;
+    for (int j = j0; j < j1; ++j) {
         const double g = gp0[baseT + j];
         if (g == 0.0) continue;
         const double C = -0.25 * g * p0[baseT + j];
@@ -377,14 +417,14 @@ __global__ void __launch_bounds__(256, 2) gv2_kernel(int M, Offsets o, const dou
             flag_status(status, ST_NOT_POSDEF);
             continue;
         }
-        const double id = 1.0 / det;
-        const double i00 = S11 * id, i01 = -S01 * id, i11 = S00 * id;  // S^{-1}
+        const double Cd = C / det;
+        const double i00 = S11 * Cd, i01 = -S01 * Cd, i11 = S00 * Cd;  // C S^{-1}
         sumC += C;
-        double cv[N][2];
+        double cv[N][2];  // C v = u (C S^{-1})
 #pragma unroll
         for (int r = 0; r < N; ++r) {
-            cv[r][0] = C * fma(uu[r][0], i00, uu[r][1] * i01);
-            cv[r][1] = C * fma(uu[r][0], i01, uu[r][1] * i11);
+            cv[r][0] = fma(uu[r][0], i00, uu[r][1] * i01);
+            cv[r][1] = fma(uu[r][0], i01, uu[r][1] * i11);
         }
         int q = 0;
 #pragma unroll
@@ -401,25 +441,19 @@ __global__ void __launch_bounds__(256, 2) gv2_kernel(int M, Offsets o, const dou
             if (g0 >= jm) atomicAdd(gV + (size_t)g0 * n2 + jm, -cv[r][1]);
             else atomicAdd(gV + (size_t)jm * n2 + g0, -cv[r][1]);
         }
-        atomicAdd(gV + (size_t)j * n2 + j, C * i00);
-        atomicAdd(gV + (size_t)(j + M) * n2 + j, C * i01);
-        atomicAdd(gV + (size_t)(j + M) * n2 + j + M, C * i11);
+        atomicAdd(gV + (size_t)j * n2 + j, i00);
+        atomicAdd(gV + (size_t)(j + M) * n2 + j, i01);
+        atomicAdd(gV + (size_t)(j + M) * n2 + j + M, i11);
     }
-    // warp reduction of the T' x T' block
-    for (int off = 16; off > 0; off >>= 1) {
-        sumC += __shfl_down_sync(0xffffffffu, sumC, off);
-#pragma unroll
-        for (int q = 0; q < NT; ++q) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off);
-    }
-    if (lane == 0 && sumC != 0.0) {
+    if (sumC != 0.0) {
         int q = 0;
 #pragma unroll
         for (int r = 0; r < N; ++r)
 #pragma unroll
             for (int c = 0; c <= r; ++c, ++q) {
                 const double v = fma(sumC, ai[q], acc[q]);
-                const int hi = gr[r] > gr[c] ? gr[r] : gr[c], lo = gr[r] > gr[c] ? gr[c] : gr[r];
-                atomicAdd(gV + (size_t)hi * n2 + lo, v);
+                const int hi2 = gr[r] > gr[c] ? gr[r] : gr[c], lo2 = gr[r] > gr[c] ? gr[c] : gr[r];
+                atomicAdd(gV + (size_t)hi2 * n2 + lo2, v);
             }
     }
 }
@@ -508,13 +542,16 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
     for (int d = 2; d <= K; ++d) {
         const uint64_t nt = binom(M, d - 1);
         const unsigned gi = (unsigned)((nt + BWD_THREADS - 1) / BWD_THREADS);
-        const unsigned gw = (unsigned)((nt * 32 + BWD_THREADS - 1) / BWD_THREADS);
+        const unsigned gw = (unsigned)((binom(M - 1, d - 1) + 127) / 128);
+        // orders 2 and 3: (prefix, 4 leaves) per thread
+        const dim3 gc((unsigned)((nt + 127) / 128), (unsigned)((M + 3) / 4));
         switch (d) {
 #define GV2_CASE(DD)                                                                                        \
     case DD:                                                                                                \
         ainv_kernel<DD - 1><<<gi, BWD_THREADS, 0, st>>>(M, f.A, a.inv, f.status);                          \
         if ((e = cudaGetLastError()) != cudaSuccess) return e;                                             \
-        gv2_kernel<DD - 1><<<gw, BWD_THREADS, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status);      \
+        if (DD <= 3) gv2_kernel<DD - 1, 4><<<gc, 128, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status); \
+        else if (gw) gv2_kernel<DD - 1, 0><<<gw, 128, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status); \
         break;
             GV2_CASE(2)
             GV2_CASE(3)

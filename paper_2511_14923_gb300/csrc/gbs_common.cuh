@@ -42,7 +42,11 @@ __device__ __forceinline__ int colex_top(uint64_t r, int k) {
     if (k == 1) return (int)r;
     float fr = (float)r;
     float est;
+    // C(c, k) ~ (c - (k-1)/2)^k / k!, so c ~ (k! r)^(1/k) + (k-1)/2; the loops
+    // below correct the estimate exactly
     if (k == 2) est = 0.5f * (1.f + sqrtf(1.f + 8.f * fr));
+    else if (k == 3) est = cbrtf(6.f * fr) + 1.f;
+    else if (k == 4) est = sqrtf(sqrtf(24.f * fr)) + 1.5f;
     else {
         float kf = 1.f;
         for (int i = 2; i <= k; ++i) kf *= (float)i;

@@ -63,7 +63,7 @@ WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm) {
     const uint64_t np0 = kmax > 1 ? order_offset(M, kmax) : 0;  // orders 1..kmax-1
     off = align256(off + sizeof(double) * (size_t)np0);
     w.scratch_off = off;
-    w.slots = (slots_per_sm > 0 ? slots_per_sm : 1) * (sms > 0 ? sms : 1);
+    w.slots = (slots_per_sm > 0 ? slots_per_sm : slots_per_sm_for(M)) * (sms > 0 ? sms : 1);
     // 2x2 blocks below the diagonal, diagonal blocks, then 2 doubles per mode for
     // the reduced half-means of a displaced state
     w.slot_doubles = 4 * ((size_t)binom2(M) + (size_t)M) + 2 * (size_t)M;

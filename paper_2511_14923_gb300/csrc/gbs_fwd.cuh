@@ -37,7 +37,8 @@ struct FwdArgs {
     int c_lo, c_hi;
     // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
     // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
-    // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area)
+    // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area, 5: 384 x 2
+    // with a 960-entry x area, 6: 256 x 4 with a 384-entry x area)
     int grain, ccap, variant;
 };
 
@@ -60,8 +61,14 @@ constexpr TreeCfg kDefaultCfg{2, 64, 0};
 constexpr int kVariant1MaxM = 577;
 // x-entries per batch of the 768-thread refined variant (one CTA per SM).
 constexpr int kWideXC = 2048;
+// x-entries per batch of the 384-thread x 2 refined variant, and its largest M.
+constexpr int kPairXC = 960;
+constexpr int kVariant5MaxM = kPairXC + 1;
+// x-entries per batch of the 256-thread x 4 refined variant, and its largest M.
+constexpr int kQuadXC = 384;
+constexpr int kVariant6MaxM = kQuadXC + 1;
 // Number of CTA shapes (variants 0..kNumVariants-1).
-constexpr int kNumVariants = 5;
+constexpr int kNumVariants = 7;
 
 // Workspace layout, shared by the size query and the launcher.
 struct WsLayout {
@@ -69,9 +76,12 @@ struct WsLayout {
     size_t slot_doubles;
     int slots;
 };
-// Reserves slots_per_sm scratch slots per multiprocessor (three cover every CTA
-// shape; with one, only the 512-thread shape runs, one CTA per multiprocessor).
-WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 3);
+// Scratch slots per multiprocessor that cover every CTA shape allowed for M:
+// four when the 256 x 4 shape can run (M <= 385), else three.
+inline int slots_per_sm_for(int M) { return M <= 385 ? 4 : 3; }
+// Reserves slots_per_sm scratch slots per multiprocessor (0 = slots_per_sm_for(M);
+// with one, only one CTA per multiprocessor runs).
+WsLayout ws_layout(int M, int kmax, int sms, int slots_per_sm = 0);
 
 // Queues the packing of A = (V+I)/2 into 2x2 blocks.
 cudaError_t launch_pack(const FwdArgs &a, cudaStream_t stream);
