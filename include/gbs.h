@@ -281,7 +281,8 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
    per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, 256 x 2
    per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, 256 x 3 when
    M <= 577, 768 x 1 with a larger shared-memory batch area, 384 x 2 when
-   M <= 961, and 256 x 4 when M <= 385) -- and records
+   M <= 961, 256 x 4 when M <= 385, and the 256 x 4 and 256 x 3 shapes in
+   thread-block clusters whose CTAs share one Schur-complement slot) -- and records
    the fastest in a process-wide table that
    later forward calls of that shape use. If the environment variable
    GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and

@@ -506,7 +506,7 @@ class Batch:
         """The batched kernel's schedule in this plan (gbs_batched_schedule)."""
         arr = (ctypes.c_int * 5)()
         _check(lib().gbs_batched_schedule(_vp(self.ws), arr))
-        shape = {0: "512x1", 1: "256x2", 2: "640x1", 3: "256x3", 4: "768x1", 5: "384x2", 6: "256x4"}.get(arr[0], str(arr[0]))
+        shape = {0: "512x1", 1: "256x2", 2: "640x1", 3: "256x3", 4: "768x1", 5: "384x2", 6: "256x4", 7: "256x4 clusters of 4", 8: "256x3 clusters of 3"}.get(arr[0], str(arr[0]))
         return {"cta_shape": shape, "threads": arr[1], "ctas": arr[2], "grain": arr[3], "children_per_batch": arr[4]}
 
     def run(self, check=False):

@@ -38,7 +38,8 @@ struct FwdArgs {
     // prefix-tree schedule (autotuned): items per CTA slot, children per shared-
     // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
     // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area, 5: 384 x 2
-    // with a 960-entry x area, 6: 256 x 4 with a 384-entry x area)
+    // with a 960-entry x area, 6: 256 x 4 with a 384-entry x area, 7: 6 in clusters
+    // of 4, 8: 3 in clusters of 3)
     int grain, ccap, variant;
 };
 
@@ -67,8 +68,11 @@ constexpr int kVariant5MaxM = kPairXC + 1;
 // x-entries per batch of the 256-thread x 4 refined variant, and its largest M.
 constexpr int kQuadXC = 384;
 constexpr int kVariant6MaxM = kQuadXC + 1;
-// Number of CTA shapes (variants 0..kNumVariants-1).
-constexpr int kNumVariants = 7;
+// Number of CTA shapes (variants 0..kNumVariants-1); 7 and 8 are the 256 x 4 and
+// 256 x 3 shapes in thread-block clusters of 4 and 3 CTAs sharing one slot.
+constexpr int kNumVariants = 9;
+// Whether a variant runs in clusters (the batched kernel has no clustered form).
+inline bool variant_clustered(int v) { return v == 7 || v == 8; }
 
 // Workspace layout, shared by the size query and the launcher.
 struct WsLayout {

@@ -83,7 +83,112 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
     }
 }
 
+// The same walk with thread-block clusters of CS CTAs: a cluster takes one U at a
+// time (its item), its CTAs build the Schur complement into the cluster's one
+// slot together and then take one stride class of the children each. Rank 0
+// draws the item and the others read it from its shared memory; three cluster
+// barriers per item (item drawn, slot built, slot released) keep every CTA of a
+// cluster on the same item sequence. One slot per cluster instead of one per
+// CTA: the slots' L2 footprint and the build work both shrink by CS.
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, int CS>
+__global__ void __launch_bounds__(NT, MINB) tree_kernel_cl(FwdArgs a, bool write_p0) {
+    using SH = TreeShared<D, XC, false>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH &sh = *reinterpret_cast<SH *>(smem_raw);
+    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int M = a.M;
+    const bool ranged = a.top != nullptr && D == a.kmax;
+    const int tlo = ranged ? a.c_lo : 0, thi = ranged ? a.c_hi : M;
+    const int c4hi = c4_max<D>(M, thi);
+    const int K = c4hi - 2 > 0 ? c4hi - 2 : 0;
+    constexpr uint64_t kWhole = 1ull << 62;  // leaves per item: one item per U
+    double *const slot = a.scratch + (size_t)(blockIdx.x / CS) * a.slot_doubles;
+    if (tid < 32) {
+        const int per = (K + 31) / 32;
+        const int lo = tid * per, hi = min(K, lo + per);
+        uint32_t sum = 0;
+        for (int k = lo; k < hi; ++k) sum += items_for_c4<D>(M, c4hi - k, kWhole, tlo, thi);
+        uint32_t incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (int k = lo; k < hi; ++k) {
+            sh.c4pref[k] = run;
+            run += items_for_c4<D>(M, c4hi - k, kWhole, tlo, thi);
+        }
+        if (tid == 31) sh.c4pref[K] = incl;
+    }
+    __syncthreads();
+    const uint32_t total_items = sh.c4pref[K];
+    uint32_t *item0 = cluster.map_shared_rank(&sh.item, 0);
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (rank == 0 && tid == 0) sh.item = atomicAdd(a.counters + D, 1u);
+        cluster.sync();  // the item is in rank 0's shared memory
+        if (tid == 0) s_item = *item0;
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= total_items) {
+            // every CTA of the cluster reads the same item, so all arrive here; no CTA
+            // leaves while another may still read rank 0's item word
+            cluster.sync();
+            break;
+        }
+        int lo = 0, hi = K;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sh.c4pref[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c4 = c4hi - lo;
+        const int u = (int)(item - sh.c4pref[lo]);
+        const int c5 = (D == 5) ? c5_first(c4, tlo) + u : M;
+        tree_item<D, MODE, PREC, NT, XC, false, true>(a, sh, slot, c4, c5, rank, CS, write_p0, a.ccap, rank, CS);
+        cluster.sync();  // every CTA is done with the slot (and with rank 0's item word)
+    }
+}
+
 // ---------------------------------------------------------------- launchers
+
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, int CS>
+static cudaError_t launch_tree_cl(const FwdArgs &a, bool write_p0, cudaStream_t st) {
+    const int M = a.M;
+    const bool ranged = a.top != nullptr && D == a.kmax;
+    const int tlo = ranged ? a.c_lo : 0, thi = ranged ? a.c_hi : M;
+    if (binom(thi, D) - binom(tlo, D) == 0) return cudaSuccess;
+    const size_t smem = sizeof(TreeShared<D, XC, false>);
+    auto fn = tree_kernel_cl<D, MODE, PREC, NT, XC, MINB, CS>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(CS * a.sms);
+    int clusters = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&clusters, (void *)fn, &cfg)) != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    if (clusters > a.slots) clusters = a.slots;
+    uint64_t items = 0;
+    for (int c4 = c4_max<D>(M, thi); c4 >= 3; --c4) items += items_for_c4<D>(M, c4, 1ull << 62, tlo, thi);
+    if (items == 0) return cudaSuccess;
+    if ((uint64_t)clusters > items) clusters = (int)items;
+    cfg.gridDim = dim3(CS * clusters);
+    e = cudaLaunchKernelEx(&cfg, fn, a, write_p0);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
 
 template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
 static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
@@ -136,6 +241,11 @@ static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t 
                 return launch_tree_v<D, MODE, PREC, 384, kPairXC, 2, false>(a, write_p0, st);
             if (a.variant == 6 && a.M <= kVariant6MaxM)
                 return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false>(a, write_p0, st);
+            // the 256 x 4 and 256 x 3 shapes in clusters that share one slot per U
+            if (a.variant == 7 && a.M <= kVariant6MaxM)
+                return launch_tree_cl<D, MODE, PREC, 256, kQuadXC, 4, 4>(a, write_p0, st);
+            if (a.variant == 8 && a.M <= kVariant1MaxM)
+                return launch_tree_cl<D, MODE, PREC, 256, 576, 3, 3>(a, write_p0, st);
         }
         return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP, 1, false>(a, write_p0, st);
     }

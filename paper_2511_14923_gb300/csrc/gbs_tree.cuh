@@ -3,6 +3,8 @@
 // functions and one work item of the prefix-tree elimination. See gbs_fwd.cu
 // for the formulas.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "gbs.h"
 #include "gbs_common.cuh"
 #include "gbs_fwd.cuh"
@@ -395,11 +397,18 @@ __device__ __forceinline__ void store_entry(const FwdArgs &a, int d, uint64_t id
 // Displaced states (DISP, FP64 only) carry the reduced half-means along: the
 // slot holds r_U(x) after the Schur blocks, the x-entries r(x) and g2(x), and
 // each leaf multiplies its P0 by exp(-r^T Sch^{-1} r).
-template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false>
+//
+// CL: the CTAs of a thread-block cluster share one slot and one U. CTA `part` of
+// `nparts` writes every nparts-th chunk of NT Schur blocks, and a cluster-wide
+// barrier (release / acquire, so the other CTAs' global writes are visible)
+// replaces the block barrier after the build; the caller passes s = part,
+// nc = nparts, so each CTA then takes one stride class of the children.
+template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false, bool CL = false>
 __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DISP> &sh, double *const slot,
                                           const int c4, const int c5, const int s, const int nc, const bool write_p0,
-                                          const int ccap = CCAP) {
+                                          const int ccap = CCAP, const int part = 0, const int nparts = 1) {
     static_assert(!DISP || PREC == 0, "displaced states run in FP64");
+    static_assert(!(DISP && CL), "displaced states run without clusters");
     using SH = TreeShared<D, XC, DISP>;
     constexpr int NP = SH::NP;
     constexpr int NQ = SH::NQ;
@@ -475,7 +484,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
         }
         __syncthreads();
         const uint32_t npairs = (uint32_t)binom2(c4);
-        for (uint32_t qi = tid; qi < npairs + (uint32_t)c4; qi += NT) {
+        for (uint32_t qi = (uint32_t)(part * NT + tid); qi < npairs + (uint32_t)c4; qi += (uint32_t)(nparts * NT)) {
             int x, y;
             if (qi < npairs) pair_decode(qi, x, y);
             else x = y = (int)(qi - npairs);
@@ -518,7 +527,8 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                 }
             }
         }
-        __syncthreads();
+        if constexpr (CL) cooperative_groups::this_cluster().sync();
+        else __syncthreads();
     }
 
     // ---- children c3 = c4-1-s, c4-1-s-nc, ... >= 2, processed in batches

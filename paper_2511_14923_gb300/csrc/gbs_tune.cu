@@ -6,7 +6,8 @@
 //   ccap    children per shared-memory batch (16 or 64),
 //   variant CTA shape: 512 threads x 1 per SM; 256 x 2 per SM (M <= 577); and for
 //           the refined path 640 x 1, 256 x 3 (M <= 577), 768 x 1 with room
-//           for more children per batch, 384 x 2 (M <= 961), or 256 x 4 (M <= 385).
+//           for more children per batch, 384 x 2 (M <= 961), 256 x 4 (M <= 385),
+//           or 256 x 4 / 256 x 3 in thread-block clusters sharing one slot.
 // Results live in a process-wide table consulted by every forward call; if the
 // environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
 // it on first use and rewritten after each tuning run (a JSON array of objects).
@@ -203,7 +204,8 @@ int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tri
     for (int variant = 0; variant <= (a.precision == 1 ? kNumVariants - 1 : 1); ++variant) {
         if ((variant == 1 || variant == 3) && a.M > kVariant1MaxM) continue;
         if (variant == 5 && a.M > kVariant5MaxM) continue;
-        if (variant == 6 && a.M > kVariant6MaxM) continue;
+        if ((variant == 6 || variant == 7) && a.M > kVariant6MaxM) continue;
+        if (variant == 8 && a.M > kVariant1MaxM) continue;
         for (int grain : {1, 2, 4, 8})
             for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, ccap, variant});
     }
