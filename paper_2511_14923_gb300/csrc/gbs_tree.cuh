@@ -259,8 +259,9 @@ template <int D, int XC = XCAP, bool DISP = false>
 struct TreeShared {
     static constexpr int NP = D - 2;       // |P|
     static constexpr int NQ = 1 << NP;     // subsets of P
-    // item decode
-    uint32_t c4pref[GBS_MAX_MODES + 2];
+    // item decode: K + 1 <= M - 2 prefix entries, M <= XC + 1 for the shapes whose
+    // x-entry area is smaller than GBS_MAX_MODES
+    uint32_t c4pref[XC < GBS_MAX_MODES ? XC + 3 : GBS_MAX_MODES + 2];
     uint32_t item;
     // uniform pivots of the item's U (and, displaced, their whitened half-means)
     double upiv[DISP ? 10 : 8];
@@ -276,19 +277,22 @@ struct TreeShared {
     double g3[DISP ? CCAP : 1][2];  // displaced: whitened half-mean of each child's c3 pivot
     // Per x-entry data, structure of arrays. FP64 path (10 double rows):
     // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
-    // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (23 float
-    // rows): z hi/lo (0-3, 4-7), d hi/lo (8-10, 11-13), c2 pivot: FP32 factor
-    // l (14-16), its inverse m (17-19), residual d - l l^T (20-22).
+    // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (6 float4
+    // rows, so that a leaf loads its x-entries with 9 vector loads, consecutive
+    // entries in consecutive 16-byte words): z hi (0), z lo (1), (d hi 00 01 11,
+    // d lo 00) (2), (d lo 01 11, c2 pivot FP32 factor l00 l10) (3), (l11, its
+    // inverse m00 m10 m11) (4), residual d - l l^T (e00 e01 e11, 0) (5).
     // Displaced states add 4 double rows: the reduced half-mean r(x) after
     // eliminating U and c3 (rows 10-11) and its whitened form g2(x) = m2(x) r(x)
     // as a c2 pivot (rows 12-13).
     // Before the batches of an item start, the same storage holds Y(x) of the
     // elimination of U (8 doubles per mode x < c4).
     static constexpr int XROWS = DISP ? 14 : 10;
-    static constexpr int XBYTES = (23 * 4 > XROWS * 8 ? 23 * 4 : XROWS * 8) * XC;
+    static constexpr int XBYTES = (6 * 16 > XROWS * 8 ? 6 * 16 : XROWS * 8) * XC;
     alignas(16) unsigned char xraw[XBYTES];
     __device__ double (*xe())[XC] { return reinterpret_cast<double(*)[XC]>(xraw); }
     __device__ float (*xf())[XC] { return reinterpret_cast<float(*)[XC]>(xraw); }
+    __device__ float4 (*xq())[XC] { return reinterpret_cast<float4(*)[XC]>(xraw); }
 };
 
 // Schur-complement slot access. FP64 path: 2x2 blocks as 4 doubles. Refined
@@ -415,6 +419,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
     constexpr int PALL = NQ - 1;
     double(*const xe)[XC] = sh.xe();
     float(*const xf)[XC] = sh.xf();
+    float4(*const xq)[XC] = sh.xq();
     const int tid = threadIdx.x;
     const int M = a.M;
     double *const sdiag = slot + 4 * binom2(M);
@@ -635,10 +640,11 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                 const DF d00 = df_sub_mul(df_sub_mul(DF{fd[0], fd[3]}, z00, z00), z10, z10);
                 const DF d01 = df_sub_mul(df_sub_mul(DF{fd[1], fd[4]}, z00, z01), z10, z11);
                 const DF d11 = df_sub_mul(df_sub_mul(DF{fd[2], fd[5]}, z01, z01), z11, z11);
-                xf[0][e] = z00.h; xf[1][e] = z01.h; xf[2][e] = z10.h; xf[3][e] = z11.h;
-                xf[4][e] = z00.l; xf[5][e] = z01.l; xf[6][e] = z10.l; xf[7][e] = z11.l;
-                xf[8][e] = d00.h; xf[9][e] = d01.h; xf[10][e] = d11.h;
-                xf[11][e] = d00.l; xf[12][e] = d01.l; xf[13][e] = d11.l;
+                xq[0][e] = make_float4(z00.h, z01.h, z10.h, z11.h);
+                xq[1][e] = make_float4(z00.l, z01.l, z10.l, z11.l);
+                xq[2][e] = make_float4(d00.h, d01.h, d11.h, d00.l);
+                float4 q3 = make_float4(d01.l, d11.l, 0.f, 0.f), q4 = make_float4(0.f, 0.f, 0.f, 0.f),
+                       q5 = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (x >= 1) {
                     // FP32 Cholesky factor of the c2 pivot d(x), its inverse, and the residual
                     // d - l l^T formed exactly (two-product, two-sum)
@@ -649,15 +655,19 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                     const float i1 = rsqrtf(pq);
                     const float l11 = pq * i1;
                     if (!(pa > 0.f) || !(pq > 0.f)) flag_status(a.status, ST_NOT_POSDEF);
-                    xf[14][e] = l00; xf[15][e] = l10; xf[16][e] = l11;
-                    xf[17][e] = i0; xf[18][e] = -l10 * i0 * i1; xf[19][e] = i1;
+                    q3.z = l00;
+                    q3.w = l10;
+                    q4 = make_float4(l11, i0, -l10 * i0 * i1, i1);
                     EftAcc r00{d00.h, d00.l}, r01{d01.h, d01.l}, r11{d11.h, d11.l};
                     eft_sub_prod(r00, l00, l00);
                     eft_sub_prod(r01, l00, l10);
                     eft_sub_prod(r11, l10, l10);
                     eft_sub_prod(r11, l11, l11);
-                    xf[20][e] = eft_val(r00); xf[21][e] = eft_val(r01); xf[22][e] = eft_val(r11);
+                    q5 = make_float4(eft_val(r00), eft_val(r01), eft_val(r11), 0.f);
                 }
+                xq[3][e] = q3;
+                xq[4][e] = q4;
+                xq[5][e] = q5;
             }
         }
         __syncthreads();
@@ -702,11 +712,13 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                     }
                     ok = det2 > 0.0;
                 } else {
-                    const DFBlk z2{xf[0][e2], xf[1][e2], xf[2][e2], xf[3][e2], xf[4][e2], xf[5][e2], xf[6][e2], xf[7][e2]};
-                    const DFBlk zj{xf[0][ej], xf[1][ej], xf[2][ej], xf[3][ej], xf[4][ej], xf[5][ej], xf[6][ej], xf[7][ej]};
-                    const DFSym dj{xf[8][ej], xf[9][ej], xf[10][ej], xf[11][ej], xf[12][ej], xf[13][ej]};
-                    const F32Piv pv{xf[14][e2], xf[15][e2], xf[16][e2], xf[17][e2], xf[18][e2],
-                                    xf[19][e2], xf[20][e2], xf[21][e2], xf[22][e2]};
+                    const float4 zh2 = xq[0][e2], zl2 = xq[1][e2], zhj = xq[0][ej], zlj = xq[1][ej];
+                    const float4 dj0 = xq[2][ej], dj1 = xq[3][ej];
+                    const float4 p3 = xq[3][e2], p4 = xq[4][e2], p5 = xq[5][e2];
+                    const DFBlk z2{zh2.x, zh2.y, zh2.z, zh2.w, zl2.x, zl2.y, zl2.z, zl2.w};
+                    const DFBlk zj{zhj.x, zhj.y, zhj.z, zhj.w, zlj.x, zlj.y, zlj.z, zlj.w};
+                    const DFSym dj{dj0.x, dj0.y, dj0.z, dj0.w, dj1.x, dj1.y};
+                    const F32Piv pv{p3.z, p3.w, p4.x, p4.y, p4.z, p4.w, p5.x, p5.y, p5.z};
                     if constexpr (MODE == MODE_KAPPA || MODE == MODE_SPINK) {
                         if (!write_p0 && a.p0f) {
                             // P0(S) is not stored: its product with P0(S') folds into the
