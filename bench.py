@@ -50,21 +50,21 @@ DTYPE = {"fp64": "f64", "fp32r": "f32 determinant steps refined to f64 accuracy;
 # Executed thread instructions per table entry of each prefix-tree kernel (ncu
 # SASS counters sm__sass_thread_inst_executed_op_{dfma,dadd,dmul,fp32}_pred_on,
 # one counter per capture, divided by the launch's entries; the M=144 kmax=5
-# cumulant call with the tuned schedules pinned: refined 256 x 4, grain 1, 64
-# children; FP64 256 x 2, grain 4, 64 children). They include the amortised
+# cumulant call with the tuned schedules pinned: refined 256 x 4, grain 2, 64
+# children; FP64 256 x 2, grain 4, 16 children). They include the amortised
 # per-item Schur-complement build and per-child eliminations. None = not captured
 # for the kernel as it stands.
 OPS_PER_ENTRY = {
-    ("fp32r", 5): {"dfma": 15.021, "dadd": 0.014, "dmul": 1.019, "fp32": 417.24},
-    ("fp32r", 4): {"dfma": 8.013, "dadd": 0.021, "dmul": 1.022, "fp32": 427.87},
-    ("fp64", 5): {"dfma": 36.149, "dadd": 0.001, "dmul": 8.406, "fp32": 4.582},
-    ("fp64", 4): {"dfma": 33.458, "dadd": 0.013, "dmul": 8.375, "fp32": 13.473},
+    ("fp32r", 5): {"dfma": 15.022, "dadd": 0.014, "dmul": 1.019, "fp32": 417.42},
+    ("fp32r", 4): {"dfma": 8.022, "dadd": 0.037, "dmul": 1.039, "fp32": 460.02},
+    ("fp64", 5): {"dfma": 36.149, "dadd": 0.001, "dmul": 8.406, "fp32": 4.592},
+    ("fp64", 4): {"dfma": 33.458, "dadd": 0.013, "dmul": 8.375, "fp32": 13.474},
 }
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # order-5 kernel at M=144 under the same pinned schedules (ncu, tree kernels
 # only, mean of the warm-up and timed launches); None once the kernel has
 # changed since the capture.
-TRAFFIC_BYTES = {"fp32r": 5.7814e9 + 4.3799e9, "fp64": 3.3383e9 + 4.2812e9}
+TRAFFIC_BYTES = {"fp32r": 5.7514e9 + 4.3314e9, "fp64": 3.3275e9 + 4.2810e9}
 NOMINAL_FP64_FMA_PER_CLK_PER_SM = 2
 NOMINAL_FP32_FMA_PER_CLK_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
