@@ -171,67 +171,130 @@ __global__ void gv_kernel(int M, Offsets o, const double *__restrict__ A, const 
 
 // gP0 by gathering: for the order-b subset B,
 //   gP0(B) = sum over R disjoint from B, |R| <= kmax - b, of g_y(B + R) h(R),
-// a group of G threads per B (G = 256 for b = 1, 32 otherwise), no atomics.
-// Term index t -> (r = |R|, colex rank of R among the r-subsets of the M - b
-// modes outside B) -> R -> B + R.
-// With chunks > 1, each B's terms are split over that many groups (group index
-// = B * chunks + chunk), and the partial sums are added atomically (gp0 zeroed).
-template <int G>
-__global__ void gp0_gather_kernel(int M, int b, int kmax, Offsets o, const double *__restrict__ gk,
-                                  const double *__restrict__ h, double *__restrict__ gp0, int chunks) {
-    const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const uint64_t unit = grp / chunks;
-    const int chunk = (int)(grp % chunks);
-    const int lane = threadIdx.x % G;
-    const uint64_t nB = binom(M, b);
-    if (unit >= nB) return;  // whole groups leave together (G divides blockDim)
-    int B[GBS_MAX_ORDER];
-    colex_unrank(unit, b, B);
-    uint64_t cum[GBS_MAX_ORDER + 2];
-    cum[0] = 0;
-    const int rmax = kmax - b;
-    for (int r = 0; r <= rmax; ++r) cum[r + 1] = cum[r] + binom(M - b, r);
-    double acc = 0.0;
-    const uint64_t nterm = cum[rmax + 1];
-    const uint64_t t0 = nterm * chunk / chunks, t1 = nterm * (chunk + 1) / chunks;
-    for (uint64_t t = t0 + lane; t < t1; t += G) {
-        int r = 0;
-        while (cum[r + 1] <= t) ++r;
-        int R[GBS_MAX_ORDER], S[GBS_MAX_ORDER];
-        if (r > 0) colex_unrank(t - cum[r], r, R);
-        // complement index -> mode: skip the elements of B (sorted)
-        for (int i = 0; i < r; ++i) {
-            int m = R[i];
-            for (int q = 0; q < b; ++q)
-                if (B[q] <= m) ++m;
-            R[i] = m;
-        }
-        // S = B + R, sorted merge
-        int ib = 0, ir = 0;
-        for (int k = 0; k < b + r; ++k) S[k] = (ir >= r || (ib < b && B[ib] < R[ir])) ? B[ib++] : R[ir++];
-        uint64_t rs = 0, rr = 0;
-        for (int k = 0; k < b + r; ++k) rs += binom(S[k], k + 1);
-        for (int k = 0; k < r; ++k) rr += binom(R[k], k + 1);
-        const double gy = (((b + r) & 1) ? -1.0 : 1.0) * gk[o.off[b + r] + rs];
-        const double hr = r ? h[o.off[r] + rr] : 1.0;
-        acc = fma(gy, hr, acc);
+// with g_y(S) = (-1)^{|S|} g(S) and h(empty) = 1.
+//
+// Each nonempty R is split as R' + {z} with z = max R, and the work unit is the
+// pair (B, R'): its thread walks z upward from max R' + 1 through the gaps of B.
+// With g elements of B below z and r = |R| = |R'| + 1, the colex ranks are
+//   rank(R' + {z})     = rank(R') + C(z, r),
+//   rank(B + R' + {z}) = c_g + C(z, r + g),
+// where c_g sums C(e, position + 1) over the other elements e of B + R'. When z
+// passes B[g], that element moves from position g + r to g + r - 1, so c_g gains
+// C(B[g], g + r) and loses C(B[g], g + r + 1). The column C(z, 0..b+r) follows z
+// by Pascal's rule, so each term costs two loads, one FMA and b + r integer adds.
+//
+// A team of T threads (a power of two) owns one B: lane l takes the units
+// l, l + T, ... of the U = sum_{s < kmax - b} C(M - b, s) sets R' (all s-subsets
+// of the modes outside B, s = |R'|, ordered by size then colex rank), and the
+// team adds its lanes in a fixed order, so the result does not depend on timing.
+
+// Sum over z of g_y(B + R' + {z}) h(R' + {z}) for one unit with |R'| = R - 1.
+template <int BB, int R>
+__device__ __forceinline__ double gather_walk(int M, const Offsets &o, const int *B, const int *Rp,
+                                              const double *__restrict__ gk, const double *__restrict__ h) {
+    const int z0 = R > 1 ? Rp[R - 2] + 1 : 0;
+    int g0 = 0;
+#pragma unroll
+    for (int k = 0; k < BB; ++k) g0 += B[k] < z0;
+    uint64_t rank_rp = 0, low = 0, high = 0;
+#pragma unroll
+    for (int i = 0; i < R - 1; ++i) {
+        int below = 0;  // elements of B below Rp[i]
+#pragma unroll
+        for (int k = 0; k < BB; ++k) below += B[k] < Rp[i];
+        rank_rp += binom(Rp[i], i + 1);
+        low += binom(Rp[i], i + below + 1);
     }
-    // group reduction
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (G == 32) {
-        if (lane == 0) {
-            if (chunks == 1) gp0[o.off[b] + unit] = acc;
-            else atomicAdd(gp0 + o.off[b] + unit, acc);
+#pragma unroll
+    for (int k = 0; k < BB; ++k) {
+        if (k < g0) {
+            int below = 0;  // elements of R' below B[k]
+#pragma unroll
+            for (int i = 0; i < R - 1; ++i) below += Rp[i] < B[k];
+            low += binom(B[k], k + below + 1);
+        } else {
+            high += binom(B[k], k + R + 1);
         }
-    } else {
-        __shared__ double red[G / 32];
-        if ((threadIdx.x & 31) == 0) red[lane >> 5] = acc;
+    }
+    uint64_t cc[BB + R + 1];  // cc[j] = C(z, j)
+#pragma unroll
+    for (int j = 0; j <= BB + R; ++j) cc[j] = binom(z0, j);
+    const double *hr = h + o.off[R] + rank_rp;
+    double t = 0.0;
+    int z = z0;
+#pragma unroll
+    for (int g = 0; g <= BB; ++g) {
+        if (g < g0) continue;
+        const int zend = g < BB ? B[g] : M;
+        const double *gs = gk + o.off[BB + R] + low + high;
+#pragma unroll 4
+        for (; z < zend; ++z) {  // unrolled: four independent gathers in flight
+            t = fma(gs[cc[R + g]], hr[cc[R]], t);
+#pragma unroll
+            for (int j = BB + R; j > 0; --j) cc[j] += cc[j - 1];
+        }
+        if (g < BB) {  // z = B[g]: step over it into the next gap
+            low += cc[g + R];
+            high -= cc[g + R + 1];
+#pragma unroll
+            for (int j = BB + R; j > 0; --j) cc[j] += cc[j - 1];
+            ++z;
+        }
+    }
+    return ((BB + R) & 1) ? -t : t;
+}
+
+template <int BB>
+__global__ void __launch_bounds__(1024) gp0_gather_kernel(int M, int kmax, Offsets o, const double *__restrict__ gk,
+                                                          const double *__restrict__ h, double *__restrict__ gp0,
+                                                          int team) {
+    const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t unit_b = gt / team;
+    const int lane = (int)(gt % team);
+    const bool live = unit_b < binom(M, BB);
+    int B[BB];
+    double acc = 0.0;
+    if (live) {
+        colex_unrank(unit_b, BB, B);
+        const int rm = kmax - BB;  // largest |R|
+        uint64_t cum[GBS_MAX_ORDER + 1];
+        cum[0] = 0;
+        for (int q = 0; q < rm; ++q) cum[q + 1] = cum[q] + binom(M - BB, q);
+        const uint64_t U = cum[rm];
+        for (uint64_t u = lane; u < U; u += team) {
+            int sz = 0;
+            while (cum[sz + 1] <= u) ++sz;
+            int Rp[GBS_MAX_ORDER];
+            if (sz > 0) colex_unrank(u - cum[sz], sz, Rp);
+            for (int i = 0; i < sz; ++i) {  // index among the modes outside B -> mode
+                int m = Rp[i];
+#pragma unroll
+                for (int k = 0; k < BB; ++k) m += B[k] <= m;
+                Rp[i] = m;
+            }
+            switch (sz + 1) {
+                case 1: acc += gather_walk<BB, 1>(M, o, B, Rp, gk, h); break;
+                case 2: if constexpr (BB + 2 <= GBS_MAX_ORDER) acc += gather_walk<BB, 2>(M, o, B, Rp, gk, h); break;
+                case 3: if constexpr (BB + 3 <= GBS_MAX_ORDER) acc += gather_walk<BB, 3>(M, o, B, Rp, gk, h); break;
+                case 4: if constexpr (BB + 4 <= GBS_MAX_ORDER) acc += gather_walk<BB, 4>(M, o, B, Rp, gk, h); break;
+                default: break;
+            }
+        }
+        if (lane == 0) acc += (BB & 1) ? -gk[o.off[BB] + unit_b] : gk[o.off[BB] + unit_b];  // R empty
+    }
+    // team sum in a fixed order
+    const int w = team < 32 ? team : 32;
+    for (int off = w / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, w);
+    if (team <= 32) {
+        if (live && lane == 0) gp0[o.off[BB] + unit_b] = acc;
+    } else {  // one team per block
+        __shared__ double red[32];
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
-        if (lane == 0) {
+        if (threadIdx.x == 0 && live) {
             double tot = 0.0;
-            for (int w = 0; w < G / 32; ++w) tot += red[w];
-            if (chunks == 1) gp0[o.off[b] + unit] = tot;
-            else atomicAdd(gp0 + o.off[b] + unit, tot);
+            for (int k = 0; k < team / 32; ++k) tot += red[k];
+            gp0[o.off[BB] + unit_b] = tot;
         }
     }
 }
@@ -513,22 +576,24 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     mark(2);
-    // 3. gP0 by gathering over supersets (one group per subset B)
+    // 3. gP0 by gathering over supersets (one team of threads per subset B)
     for (int b = 1; b <= K; ++b) {
         const uint64_t n = binom(M, b);
         if (b == K) {
             gp0_top_kernel<<<(unsigned)((n + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(
                 n, (K & 1) ? -1.0 : 1.0, a.gk + o.off[K], a.gp0 + o.off[K]);
-        } else if (b == 1) {
-            // few units with many terms each: split each B over several CTAs
-            int chunks = (int)((4 * (uint64_t)a.fwd.sms + n - 1) / n);
-            if (chunks < 1) chunks = 1;
-            if ((e = cudaMemsetAsync(a.gp0, 0, sizeof(double) * n, st)) != cudaSuccess) return e;
-            gp0_gather_kernel<256><<<(unsigned)(n * chunks), 256, 0, st>>>(M, b, K, o, a.gk, a.h, a.gp0, chunks);
         } else {
-            const uint64_t thr = n * 32;
-            gp0_gather_kernel<32><<<(unsigned)((thr + BWD_THREADS - 1) / BWD_THREADS), BWD_THREADS, 0, st>>>(
-                M, b, K, o, a.gk, a.h, a.gp0, 1);
+            // team size: about four units per lane, at most one block per B
+            uint64_t units = 0;
+            for (int q = 0; q < K - b; ++q) units += binom(M - b, q);
+            int team = 1;
+            while (team < 1024 && 4 * (uint64_t)team < units) team *= 2;
+            const int nt = team > 32 ? team : 256;  // a team wider than a warp fills its block
+            const unsigned gl = (unsigned)((n * team + nt - 1) / nt);
+            if (b == 1) gp0_gather_kernel<1><<<gl, nt, 0, st>>>(M, K, o, a.gk, a.h, a.gp0, team);
+            else if (b == 2) gp0_gather_kernel<2><<<gl, nt, 0, st>>>(M, K, o, a.gk, a.h, a.gp0, team);
+            else if (b == 3) gp0_gather_kernel<3><<<gl, nt, 0, st>>>(M, K, o, a.gk, a.h, a.gp0, team);
+            else gp0_gather_kernel<4><<<gl, nt, 0, st>>>(M, K, o, a.gk, a.h, a.gp0, team);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -584,24 +649,57 @@ __device__ __forceinline__ double qdiag(const double *r, int M, int k) {
     return k < M ? exp(-2.0 * r[k]) : exp(2.0 * r[k - M]);
 }
 
-__device__ __forceinline__ double wmat(const double *Ur, const double *Ui, const double *r, int M, int a, int b) {
-    double acc = 0.0;
-    for (int k = 0; k < 2 * M; ++k) acc = fma(smat(Ur, Ui, M, a, k) * qdiag(r, M, k), smat(Ur, Ui, M, b, k), acc);
-    return acc;
-}
+// V = D (S Q S^T) D + I - D^2 with D = diag(sqrt(eta)) (eta repeated for the
+// x and p blocks), Q = diag(e^{-2r}, e^{2r}): a 2M x 2M symmetric product, tiled
+// 32 x 32. Each block computes one tile on or below the diagonal (256 threads,
+// four rows each) and writes it and its mirror; the k dimension advances 32 at
+// a time through shared memory, with the 32 entries of Q of that step computed
+// once per block.
+constexpr int COV_TILE = 32;
 
-__global__ void covariance_kernel(const double *Ur, const double *Ui, const double *r, const double *eta, int M,
-                                  double *V) {
+__global__ void __launch_bounds__(256) covariance_kernel(const double *Ur, const double *Ui, const double *r,
+                                                         const double *eta, int M, double *V) {
+    __shared__ double As[COV_TILE][COV_TILE + 1], Bs[COV_TILE][COV_TILE + 1];
     const int n2 = 2 * M;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n2 * n2) return;
-    const int a = idx / n2, b = idx - a * n2;
-    if (b > a) return;  // lower triangle computes, mirror writes
-    const double da = sqrt(eta[a < M ? a : a - M]), db = sqrt(eta[b < M ? b : b - M]);
-    double v = da * wmat(Ur, Ui, r, M, a, b) * db;
-    if (a == b) v += 1.0 - da * da;
-    V[(size_t)a * n2 + b] = v;
-    V[(size_t)b * n2 + a] = v;
+    // block -> tile (ta, tb) with tb <= ta
+    int ta = (int)((sqrt(8.0 * blockIdx.x + 1.0) - 1.0) * 0.5);
+    while ((ta + 1) * (ta + 2) / 2 <= (int)blockIdx.x) ++ta;
+    while (ta * (ta + 1) / 2 > (int)blockIdx.x) --ta;
+    const int tb = (int)blockIdx.x - ta * (ta + 1) / 2;
+    const int a0 = ta * COV_TILE, b0 = tb * COV_TILE;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < n2; k0 += COV_TILE) {
+        const int k = k0 + tx;
+        const double q = k < n2 ? qdiag(r, M, k) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int row = ty + 8 * u;
+            As[row][tx] = (a0 + row < n2 && k < n2) ? smat(Ur, Ui, M, a0 + row, k) * q : 0.0;
+            Bs[row][tx] = (b0 + row < n2 && k < n2) ? smat(Ur, Ui, M, b0 + row, k) : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < COV_TILE; ++kk) {
+            const double bv = Bs[tx][kk];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(As[ty + 8 * u][kk], bv, acc[u]);
+        }
+        __syncthreads();
+    }
+    const int b = b0 + tx;
+    if (b >= n2) return;
+    const double db = sqrt(eta[b < M ? b : b - M]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int a = a0 + ty + 8 * u;
+        if (a >= n2 || b > a) continue;
+        const double da = sqrt(eta[a < M ? a : a - M]);
+        double v = da * acc[u] * db;
+        if (a == b) v += 1.0 - da * da;
+        V[(size_t)a * n2 + b] = v;
+        V[(size_t)b * n2 + a] = v;
+    }
 }
 
 // One block per mode i, threads over rows a (and columns b for eta):
@@ -610,19 +708,27 @@ __global__ void covariance_kernel(const double *Ur, const double *Ui, const doub
 // (the second uses W_ab D_b = (V_ab - delta_ab (1 - D_a^2)) / D_a).
 __global__ void covariance_bwd_kernel(const double *Ur, const double *Ui, const double *r, const double *eta, int M,
                                       const double *V, const double *G, double *dr, double *deta) {
+    extern __shared__ double cov_sh[];  // columns i and i + M of D S: 2 x 2M doubles
     const int n2 = 2 * M;
     const int i = blockIdx.x;
+    double *ds0 = cov_sh, *ds1 = cov_sh + n2;
+    for (int b = threadIdx.x; b < n2; b += blockDim.x) {
+        const double db = sqrt(eta[b < M ? b : b - M]);
+        ds0[b] = db * smat(Ur, Ui, M, b, i);
+        ds1[b] = db * smat(Ur, Ui, M, b, i + M);
+    }
+    __syncthreads();
     double hx = 0.0, hp = 0.0, te = 0.0;
     for (int a = threadIdx.x; a < n2; a += blockDim.x) {
         double tx = 0.0, tp = 0.0;
+        const double *Ga = G + (size_t)a * n2;
         for (int b = 0; b < n2; ++b) {
-            const double gab = G[(size_t)a * n2 + b] * sqrt(eta[b < M ? b : b - M]);
-            tx = fma(gab, smat(Ur, Ui, M, b, i), tx);
-            tp = fma(gab, smat(Ur, Ui, M, b, i + M), tp);
+            const double gab = Ga[b];
+            tx = fma(gab, ds0[b], tx);
+            tp = fma(gab, ds1[b], tp);
         }
-        const double da = sqrt(eta[a < M ? a : a - M]);
-        hx = fma(smat(Ur, Ui, M, a, i) * da, tx, hx);
-        hp = fma(smat(Ur, Ui, M, a, i + M) * da, tp, hp);
+        hx = fma(ds0[a], tx, hx);
+        hp = fma(ds1[a], tp, hp);
         // eta term, thread a plays the column b
         for (int q = 0; q < 2; ++q) {
             const int ra = i + q * M;
@@ -657,14 +763,20 @@ __global__ void covariance_bwd_kernel(const double *Ur, const double *Ui, const 
 
 cudaError_t launch_covariance(const double *Ur, const double *Ui, const double *r, const double *eta, int M, double *V,
                               cudaStream_t st) {
-    const int n = 4 * M * M;
-    covariance_kernel<<<(n + 255) / 256, 256, 0, st>>>(Ur, Ui, r, eta, M, V);
+    const int nt = (2 * M + COV_TILE - 1) / COV_TILE;
+    covariance_kernel<<<nt * (nt + 1) / 2, 256, 0, st>>>(Ur, Ui, r, eta, M, V);
     return cudaGetLastError();
 }
 
 cudaError_t launch_covariance_bwd(const double *Ur, const double *Ui, const double *r, const double *eta, int M,
                                   const double *V, const double *G, double *dr, double *deta, cudaStream_t st) {
-    covariance_bwd_kernel<<<M, 256, 0, st>>>(Ur, Ui, r, eta, M, V, G, dr, deta);
+    const size_t smem = sizeof(double) * 4 * (size_t)M;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(covariance_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    covariance_bwd_kernel<<<M, 256, smem, st>>>(Ur, Ui, r, eta, M, V, G, dr, deta);
     return cudaGetLastError();
 }
 

@@ -69,10 +69,11 @@ def test_covariance_kernel_matches_model():
     assert np.abs(V - inst.V).max() <= 1e-12 * np.abs(inst.V).max()
 
 
-def test_covariance_adjoint_matches_oracle_chain():
-    inst = synthetic.random_instance(20, 3, seed=11)
-    rng = np.random.default_rng(2)
-    G = rng.standard_normal((40, 40)); G = G + G.T
+@pytest.mark.parametrize("M,seed", [(20, 11), (3, 12), (37, 13)])
+def test_covariance_adjoint_matches_oracle_chain(M, seed):
+    inst = synthetic.random_instance(M, 3, seed=seed)
+    rng = np.random.default_rng(seed - 9)
+    G = rng.standard_normal((2 * M, 2 * M)); G = G + G.T
     U = torch.from_numpy(inst.U).cuda()
     dr, de = gbs.covariance_backward(U, cuda(inst.r), cuda(inst.eta), cuda(inst.V), cuda(G))
     rr, re = oracle.chain_to_params(G, inst.r, inst.eta, inst.U)
@@ -123,3 +124,13 @@ def test_adjoint_closed_form_single_squeezer():
     kt = gbs.CumulantFn.apply(V, 1)
     (1.0 - kt[0]).backward()   # P0 = 1 - kt({0})
     assert r.grad.item() == pytest.approx(-np.tanh(r0) / np.cosh(r0), rel=1e-12)
+
+
+@pytest.mark.parametrize("M,seed", [(1, 21), (7, 22), (16, 23), (37, 24)])
+def test_covariance_kernel_ragged_tiles(M, seed):
+    """The covariance kernel's 32 x 32 tiles: one partial tile, an exact fit
+    (2M = 32) and a ragged edge over several tiles."""
+    inst = synthetic.random_instance(M, 1, seed=seed, r_range=(0.2, 1.1), eta_range=(0.3, 0.9))
+    U = torch.from_numpy(inst.U).cuda()
+    V = gbs.covariance(U, cuda(inst.r), cuda(inst.eta)).cpu().numpy()
+    assert np.abs(V - inst.V).max() <= 1e-12 * np.abs(inst.V).max()
