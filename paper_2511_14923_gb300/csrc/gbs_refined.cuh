@@ -47,6 +47,18 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return __longlong_as_double((long long)(e == 0u ? sign : r));
 }
 
+// FP64 value truncated to FP32 (toward zero: relative error below 2^-23),
+// assembled from its bits on the integer pipe. Finite inputs in FP32's normal
+// range only; any other input (zero, below 2^-126, at or above 2^128, inf, NaN)
+// gives 0.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned r = (hi & 0x80000000u) | ((unsigned)e << 23) | m;
+    return (e > 0 && e < 255) ? __uint_as_float(r) : 0.f;
+}
+
 // Double-float (unevaluated FP32 pair) arithmetic on the FP32 pipe, after Dekker
 // and Knuth: products split exactly by an FMA, sums by two-sum. Relative
 // accuracy about 2^-47 per operation.
@@ -220,9 +232,13 @@ __device__ __forceinline__ double refined_leaf_p0(double P0Sp, const DFBlk &S, c
 // leading term of the cumulant recursion when P0(S) itself is not stored, with
 // p = P0({j}) given as an FP32 pair (ph + pl). The difference
 // w = r0 - ph + r0 eta - pl is formed on the FP32 pipe as an unevaluated pair
-// (two-sum of r0 - ph, which is exact when they are close, plus the exact
-// product r0 eta), so only the two products with P0(S') run in FP64: one FP64
-// instruction fewer than forming P0(S) first. The sign goes into the FP32 bits.
+// s + lo (two-sum of r0 - ph, which is exact when they are close, plus the exact
+// product r0 eta). Then P0(S') w = P0(S') s + P0(S') lo takes one FP64 FMA: the
+// second product is a correction about 2^-24 below the first, so it is formed
+// in FP32 from P0(S') truncated to FP32 (relative error below 2^-23 on a term
+// of relative size 2^-24) and enters as the FMA's addend. P0(S') below FP32's
+// normal range drops the correction (an absolute error under 1e-45). The sign
+// goes into the FP32 bits.
 template <bool NEG>
 __device__ __forceinline__ double refined_lead_term(double P0Sp, float r0, float eta, float ph, float pl) {
     const float s = __fadd_rn(r0, -ph);
@@ -231,9 +247,10 @@ __device__ __forceinline__ double refined_lead_term(double P0Sp, float r0, float
     const float pr = r0 * eta;
     const float qr = __fmaf_rn(r0, eta, -pr);
     const float lo = __fadd_rn(__fadd_rn(e1, -pl), __fadd_rn(pr, qr));
+    const float c = d2f_bits(P0Sp) * lo;
     const unsigned flip = NEG ? 0x80000000u : 0u;
-    return fma(P0Sp, f2d_bits(__uint_as_float(__float_as_uint(lo) ^ flip)),
-               P0Sp * f2d_bits(__uint_as_float(__float_as_uint(s) ^ flip)));
+    return fma(P0Sp, f2d_bits(__uint_as_float(__float_as_uint(s) ^ flip)),
+               f2d_bits(__uint_as_float(__float_as_uint(c) ^ flip)));
 }
 
 }  // namespace gbs

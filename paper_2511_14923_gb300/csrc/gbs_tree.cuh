@@ -722,7 +722,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                     if constexpr (MODE == MODE_KAPPA || MODE == MODE_SPINK) {
                         if (!write_p0 && a.p0f) {
                             // P0(S) is not stored: its product with P0(S') folds into the
-                            // recursion's leading term (16 FP64 instructions per entry)
+                            // recursion's leading term (15 FP64 instructions per entry)
                             float r0, eta;
                             refined_leaf_factor(Sdf, z2, zj, dj, pv, r0, eta, ok);
                             const float2 pj = reinterpret_cast<const float2 *>(a.p0f)[j];
