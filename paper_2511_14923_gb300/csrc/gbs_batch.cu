@@ -199,6 +199,7 @@ __device__ void tree_phase(const PlanHdr &h, const InstDev *inst, const uint64_t
                            unsigned *status, unsigned *counters, double *slot, unsigned char *smem) {
     TreeShared<D, XC> &sh = *reinterpret_cast<TreeShared<D, XC> *>(smem);
     __shared__ int s_dec[6];
+    __shared__ FwdArgs s_args;
     const int n = h.n;
     const uint64_t *pf = pref + (size_t)D * (n + 1);
     const uint64_t total = h.total[D];
@@ -227,6 +228,7 @@ __device__ void tree_phase(const PlanHdr &h, const InstDev *inst, const uint64_t
                 s_dec[2] = D == 5 ? c4 + 1 + (int)(rr / nc) : I.M;
                 s_dec[3] = (int)(rr % nc);
                 s_dec[4] = nc;
+                s_args = inst_args(I, status, nullptr, h.slot_doubles, PREC);
             }
         }
         __syncthreads();
@@ -234,9 +236,8 @@ __device__ void tree_phase(const PlanHdr &h, const InstDev *inst, const uint64_t
         const int c4 = s_dec[1], c5 = s_dec[2], s = s_dec[3], nc = s_dec[4];
         __syncthreads();
         if (i < 0) break;
-        const InstDev &I = inst[i];
-        const FwdArgs a = inst_args(I, status, nullptr, h.slot_doubles, PREC);
-        tree_item<D, MODE_KAPPA, PREC, NT, XC>(a, sh, slot, c4, c5, s, nc, D < I.kmax, h.ccap);
+        tree_item<D, MODE_KAPPA, PREC, NT, XC>(s_args, sh, slot, c4, c5, s, nc, D < GBS_MAX_ORDER && D < s_args.kmax,
+                                               h.ccap);
     }
 }
 
