@@ -449,6 +449,7 @@ def run_fit(steps, warmup, peaks):
             e.record()
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    gbs.check_pending()  # the autograd Functions' deferred device-status checks
     # the adjoint's phases (one more call with the library's events on)
     V = gbs.covariance(U, r.detach(), eta.detach())
     g = torch.randn(gbs.table_size(M, K), dtype=torch.float64, device="cuda")

@@ -108,6 +108,14 @@ const char *gbs_last_error(void);
    the next compute call that uses the workspace. */
 int gbs_stream_status(const void *workspace, void *cuda_stream);
 
+/* The gbs_status that a status word (the first 4 bytes of a workspace, as a
+   compute call leaves them) stands for, with its message for gbs_last_error():
+   GBS_OK for 0, else GBS_ERR_TIMEOUT, GBS_ERR_NOT_POSDEF or GBS_ERR_INVALID_ARG
+   (a failed device index check), in that order of precedence. Host-only, no
+   CUDA call: it lets a caller copy the word to host memory asynchronously
+   (stream-ordered, no synchronisation) and interpret it when the copy is done. */
+int gbs_status_code(unsigned status_word);
+
 /* Spin-correlator table: c_out[...] <- c(S) = E[prod_{k in S} (-1)^{x_k}]
    = (-1)^{|S|} sum_{R subset S} (-2)^{|R|} P0(R)  (Eq. correlator_sum_cov, hbar = 2),
    the correlators the paper's stage 1 computes. */

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
     L.gbs_workspace_bytes.argtypes = [i32, i32, i32]; L.gbs_workspace_bytes.restype = sz
     L.gbs_last_error.argtypes = []; L.gbs_last_error.restype = ctypes.c_char_p
     L.gbs_stream_status.argtypes = [vp, vp]; L.gbs_stream_status.restype = i32
+    L.gbs_status_code.argtypes = [ctypes.c_uint]; L.gbs_status_code.restype = i32
     L.gbs_autotune.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp, ctypes.POINTER(ctypes.c_float)]
     L.gbs_autotune.restype = i32
     L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
@@ -106,6 +107,47 @@ def lib() -> ctypes.CDLL:
 def _check(rc: int):
     if rc != 0:
         raise GbsError(rc, lib().gbs_last_error().decode())
+
+
+# Deferred device-status checks (check="defer"): the call's status word is copied
+# to pinned host memory on its stream (no synchronisation) and read once that
+# copy has completed -- at the next library call from this process, or in
+# check_pending(). Entries: (event after the copy, pinned int32[1], call name).
+_pending: list = []
+
+
+def _defer_status(ws: torch.Tensor, stream, what: str):
+    """Queue the status word (first 4 bytes of the workspace tensor ws) for a
+    deferred check, after raising for any earlier deferred call that failed."""
+    check_pending(wait=False)
+    word = ws.reshape(-1).view(torch.uint8)[:4].view(torch.int32)
+    host = torch.empty(1, dtype=torch.int32, pin_memory=True)
+    with torch.cuda.stream(stream):
+        host.copy_(word, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+    _pending.append((ev, host, what))
+
+
+def check_pending(wait: bool = True):
+    """Raise GbsError for the first failed call among those queued with
+    check="defer" whose status word has arrived (with wait=True, after waiting
+    for every queued copy). Calls whose status has been read are dropped."""
+    global _pending
+    keep, failed = [], None
+    for ev, host, what in _pending:
+        if wait:
+            ev.synchronize()
+        if not ev.query():
+            keep.append((ev, host, what))
+            continue
+        if failed is None:
+            rc = int(lib().gbs_status_code(ctypes.c_uint(int(host.item()) & 0xFFFFFFFF)))
+            if rc != 0:
+                failed = GbsError(rc, f"{what}: " + lib().gbs_last_error().decode())
+    _pending = keep
+    if failed is not None:
+        raise failed
 
 
 def table_size(M: int, kmax: int) -> int:
@@ -202,7 +244,9 @@ def _prep(V: torch.Tensor):
     return V.contiguous(), V.shape[0] // 2
 
 
-def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, workspace, check: bool):
+def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, workspace, check):
+    """check: True = synchronise and raise on a device error; "defer" = queue the
+    status for check_pending(); False = leave it in the workspace."""
     V, M = _prep(V)
     n = table_size(M, kmax)
     if n == 0:
@@ -217,7 +261,9 @@ def _forward(fname: str, V: torch.Tensor, kmax: int, precision: str, out, worksp
     f = getattr(lib(), fname)
     _check(f(ctypes.c_void_p(V.data_ptr()), M, kmax, ctypes.c_void_p(out.data_ptr()), PRECISIONS[precision],
              ctypes.c_void_p(ws.ptr), ws.nbytes, ctypes.c_void_p(st.cuda_stream)))
-    if check:
+    if check == "defer":
+        _defer_status(ws.buf, st, fname)
+    elif check:
         _check(ws.status(st))
     return out
 
@@ -388,7 +434,9 @@ def cumulants_backward(V, kmax, grad_kappa, workspace: torch.Tensor | None = Non
     st = torch.cuda.current_stream(V.device)
     _check(lib().gbs_cumulants_backward(_vp(V), M, kmax, _vp(g), _vp(out), _vp(ws), _nbytes(ws),
                                         ctypes.c_void_p(st.cuda_stream)))
-    if check:
+    if check == "defer":
+        _defer_status(ws, st, "gbs_cumulants_backward")
+    elif check:
         _check(lib().gbs_stream_status(_vp(ws), ctypes.c_void_p(st.cuda_stream)))
     return out
 
@@ -417,18 +465,22 @@ def covariance_backward(U, r, eta, V, grad_V):
 
 
 class CumulantFn(torch.autograd.Function):
-    """kt = cumulants(V); backward through gbs_cumulants_backward."""
+    """kt = cumulants(V); backward through gbs_cumulants_backward.
+
+    Neither pass synchronises the stream: device errors (a reduced covariance that
+    is not positive definite) are checked with check="defer" and raise GbsError at
+    a later library call or in check_pending(); the affected entries are NaN."""
 
     @staticmethod
     def forward(ctx, V, kmax, precision="fp64"):
         ctx.save_for_backward(V)
         ctx.kmax = kmax
-        return cumulants(V, kmax, precision)
+        return cumulants(V, kmax, precision, check="defer")
 
     @staticmethod
     def backward(ctx, g):
         (V,) = ctx.saved_tensors
-        return cumulants_backward(V, ctx.kmax, g.contiguous()), None, None
+        return cumulants_backward(V, ctx.kmax, g.contiguous(), check="defer"), None, None
 
 
 class CovarianceFn(torch.autograd.Function):

@@ -258,6 +258,10 @@ int gbs_stream_status(const void *workspace, void *cuda_stream) {
     unsigned s = 0;
     e = cudaMemcpy(&s, workspace, sizeof s, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(GBS_ERR_CUDA, "reading the status word: %s", cudaGetErrorString(e));
+    return gbs_status_code(s);
+}
+
+int gbs_status_code(unsigned s) {
     if (s & gbs::ST_TIMEOUT) return fail(GBS_ERR_TIMEOUT, "a bounded device wait gave up");
     if (s & gbs::ST_NOT_POSDEF)
         return fail(GBS_ERR_NOT_POSDEF, "a reduced covariance (V_T + I)/2 is not positive definite");

@@ -143,3 +143,15 @@ def test_python_workspace_checks_run_before_any_library_call():
     assert gbs._on(t, torch.device("cpu"), "t") is t
     with pytest.raises(ValueError):
         gbs._on(t, torch.device("meta"), "t")
+
+
+def test_status_code_maps_status_words():
+    """gbs_status_code interprets a status word copied to the host without a
+    synchronisation (the deferred checks of the autograd Functions): the bits
+    not-positive-definite (1), bounded-wait timeout (2) and device index check
+    (4), timeout first."""
+    f = gbs.lib().gbs_status_code
+    assert f(0) == 0 and gbs.lib().gbs_last_error() == b""
+    assert f(1) == 2 and b"positive definite" in gbs.lib().gbs_last_error()
+    assert f(2) == 4 and f(3) == 4 and f(7) == 4
+    assert f(4) == 1 and f(5) == 2

@@ -134,3 +134,23 @@ def test_covariance_kernel_ragged_tiles(M, seed):
     U = torch.from_numpy(inst.U).cuda()
     V = gbs.covariance(U, cuda(inst.r), cuda(inst.eta)).cpu().numpy()
     assert np.abs(V - inst.V).max() <= 1e-12 * np.abs(inst.V).max()
+
+
+def test_autograd_functions_defer_device_errors():
+    """CumulantFn queues its device status instead of synchronising: a reduced
+    covariance that is not positive definite gives NaN entries at once and a
+    GbsError (not positive definite) from check_pending; a clean call after it
+    leaves nothing pending."""
+    inst = synthetic.random_instance(12, 3, seed=41)
+    bad = cuda(inst.V).clone()
+    bad[2, 2] = -5.0
+    kt = gbs.CumulantFn.apply(bad, 3)  # no exception here
+    assert torch.isnan(kt).any()
+    with pytest.raises(gbs.GbsError) as err:
+        gbs.check_pending()
+    assert err.value.code == 2
+    V = cuda(inst.V).requires_grad_(True)
+    kt = gbs.CumulantFn.apply(V, 3)
+    (g,) = torch.autograd.grad(kt.sum(), (V,))
+    gbs.check_pending()
+    assert torch.isfinite(g).all()
