@@ -422,7 +422,8 @@ def _dev64(t: torch.Tensor, name: str) -> torch.Tensor:
 
 
 def cumulants_backward(V, kmax, grad_kappa, workspace: torch.Tensor | None = None, check=True):
-    """dL/dV (2M x 2M, symmetric) from dL/dkt (table layout), FP64."""
+    """dL/dV (2M x 2M, symmetric) from dL/dkt (table layout); FP64 sums, refined P0
+    and double-float inverses (see gbs_cumulants_backward in gbs.h)."""
     V, M = _prep(V)
     g = _on(_dev64(grad_kappa, "grad_kappa"), V.device, "grad_kappa")
     n = table_size(M, kmax)

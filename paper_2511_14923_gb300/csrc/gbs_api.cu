@@ -303,7 +303,13 @@ int gbs_cumulants_backward(const double *V, int M, int kmax, const double *grad_
     a.M = M;
     a.kmax = kmax;
     a.mode = gbs::MODE_P0;
-    a.precision = GBS_FP64;
+    a.precision = GBS_FP32_REFINED;  // the P0 recomputation (launch_backward)
+    {
+        const gbs::TreeCfg cfg = gbs::tuned_cfg(sms, M, kmax, GBS_FP32_REFINED);
+        a.grain = cfg.grain;
+        a.ccap = cfg.ccap;
+        a.variant = cfg.variant;
+    }
     a.A = reinterpret_cast<double *>(w + L.fwd.A_off);
     a.Af = reinterpret_cast<float *>(a.A + 4 * (size_t)M * M);
     a.status = reinterpret_cast<unsigned *>(w + L.fwd.status_off);

@@ -22,6 +22,7 @@
 #include "gbs.h"
 #include "gbs_bwd.cuh"
 #include "gbs_common.cuh"
+#include "gbs_refined.cuh"
 
 namespace gbs {
 
@@ -375,14 +376,11 @@ __global__ void ainv_kernel(int M, const double *__restrict__ A, double *__restr
 // Each contribution is C(T) A_T^{-1}, C(T) = -1/4 gP0(T) P0(T). The thread keeps
 // A'^{-1} and the T' x T' block's running sum (sum_j C) A'^{-1} + sum_j C v u^T
 // in registers and adds the block once; the j rows go straight to dV.
-// With L = 0 a thread takes all leaves of its prefix. Prefixes are then
-// numbered by their smallest element s0 (the C(M-1-s0, DP-1) of them with
-// smallest element s0 follow the C(M-1, DP) - C(M-s0, DP) with a smaller one,
-// s0 >= 1), so the threads of a warp share s0 and the trip count; the largest s0
-// come first (thread gi takes prefix n - 1 - gi). With L > 0 (the low orders,
-// whose few prefixes would leave most of the GPU idle), thread x of grid row y
-// takes leaves [y L, y L + L) of the prefix of colex rank x, and adds its part of
-// the T' x T' block on its own.
+// The low orders, whose few prefixes would leave most of the GPU idle, split
+// each prefix's leaves: thread x of grid row y takes leaves [y L, y L + L) of the
+// prefix of colex rank x and adds its part of the T' x T' block on its own. The
+// higher orders (one thread per prefix walking all its leaves) run the same
+// update in double-float arithmetic (gv2df_kernel).
 template <int DP, int L>
 __global__ void __launch_bounds__(128) gv2_kernel(int M, Offsets o, const double *__restrict__ A,
                                                   const double *__restrict__ p0, const double *__restrict__ gp0,
@@ -391,28 +389,8 @@ __global__ void __launch_bounds__(128) gv2_kernel(int M, Offsets o, const double
     constexpr int N = 2 * DP, NT = N * (N + 1) / 2, D = DP + 1;
     int s[DP];
     int j0, j1;
-    if constexpr (L == 0) {
-        const uint64_t nthr = binom(M - 1, DP);
-        const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (gi >= nthr) return;
-        const uint64_t i = nthr - 1 - gi;
-        // s0: the last s in [1, M - DP] with C(M-1, DP) - C(M-s, DP) <= i
-        int lo = 1, hi = M - DP + 1;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (nthr - binom(M - mid, DP) <= i) lo = mid;
-            else hi = mid;
-        }
-        s[0] = lo;
-        if constexpr (DP > 1) {
-            int e[DP - 1];
-            colex_unrank(i - (nthr - binom(M - lo, DP)), DP - 1, e);
-#pragma unroll
-            for (int k = 0; k < DP - 1; ++k) s[k + 1] = lo + 1 + e[k];
-        }
-        j0 = 0;
-        j1 = s[0];
-    } else {
+    static_assert(L > 0, "chunked leaves only");
+    {
         const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
         if (w >= binom(M, DP)) return;
         colex_unrank(w, DP, s);
@@ -521,6 +499,218 @@ __global__ void __launch_bounds__(128) gv2_kernel(int M, Offsets o, const double
     }
 }
 
+// ---------------------------------------------------------------- double-float scatter
+// The dL/dV scatter of the orders whose prefixes are numerous (one thread per
+// prefix, gv2_kernel<DP, 0>) in double-float arithmetic on the FP32 pipe: the
+// same block-inverse update, each FP64 product replaced by an unevaluated FP32
+// pair (about 2^-44 relative per operation; GB300's FP32 pipe issues 62 times the
+// FP64 pipe's FMAs). Inputs come from the float-pair copy of A and from FP64
+// tables (A_{T'}^{-1} split once per prefix); each result is rounded to FP64
+// once, for its atomic add.
+
+// s + t, not normalised: a dot product's running sum (t gathers the rounding
+// errors of the two-sums and the low parts of the products).
+struct DFAcc {
+    float s, t;
+};
+
+__device__ __forceinline__ void dfa_fma(DFAcc &acc, DF a, DF b) {  // acc += a b
+    const float p = a.h * b.h;
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    const float s = __fadd_rn(acc.s, p);
+    const float bb = __fsub_rn(s, acc.s);
+    const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.s = s;
+    acc.t = __fadd_rn(acc.t, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ DF dfa_val(DFAcc a) {  // two-sum s + t
+    const float r = __fadd_rn(a.s, a.t);
+    const float bb = __fsub_rn(r, a.s);
+    return DF{r, __fadd_rn(__fsub_rn(a.s, __fsub_rn(r, bb)), __fsub_rn(a.t, bb))};
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+
+__device__ __forceinline__ DF df_prod(DF a, DF b) {
+    DFAcc z{0.f, 0.f};
+    dfa_fma(z, a, b);
+    return dfa_val(z);
+}
+
+// a / b for b > 0: an FP32 quotient, corrected once by the exact residual a - q b.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float rb = __frcp_rn(b.h);
+    const float q1 = a.h * rb;
+    DFAcc r{a.h, a.l};
+    dfa_fma(r, DF{-q1, 0.f}, b);
+    const float q2 = __fadd_rn(r.s, r.t) * rb;
+    const float q = __fadd_rn(q1, q2);
+    return DF{q, __fsub_rn(q2, __fsub_rn(q, q1))};
+}
+
+__device__ __forceinline__ DF df_of(double x) {
+    DF r;
+    split_df(x, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+
+// One thread per prefix T' walking all its leaves j < s0 = min T' (the block
+// inverse update of gv2_kernel). Prefixes are numbered by their smallest element
+// s0 (the C(M-1-s0, DP-1) of them with smallest element s0 follow the
+// C(M-1, DP) - C(M-s0, DP) with a smaller one, s0 >= 1), so the threads of a warp
+// share s0 and the trip count; the largest s0 come first (thread gi takes prefix
+// n - 1 - gi).
+template <int DP>
+__global__ void __launch_bounds__(128) gv2df_kernel(int M, Offsets o, const float *__restrict__ Af,
+                                                    const double *__restrict__ p0, const double *__restrict__ gp0,
+                                                    const double *__restrict__ inv, double *__restrict__ gV,
+                                                    unsigned *status) {
+    constexpr int N = 2 * DP, NT = N * (N + 1) / 2, D = DP + 1;
+    int s[DP];
+    const uint64_t nthr = binom(M - 1, DP);
+    const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= nthr) return;
+    const uint64_t i = nthr - 1 - gi;
+    int lo = 1, hi = M - DP + 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (nthr - binom(M - mid, DP) <= i) lo = mid;
+        else hi = mid;
+    }
+    s[0] = lo;
+    if constexpr (DP > 1) {
+        int e[DP - 1];
+        colex_unrank(i - (nthr - binom(M - lo, DP)), DP - 1, e);
+#pragma unroll
+        for (int k = 0; k < DP - 1; ++k) s[k + 1] = lo + 1 + e[k];
+    }
+    const int s0 = s[0];
+    const int n2 = 2 * M;
+    uint64_t w = 0;
+#pragma unroll
+    for (int u = 0; u < DP; ++u) w += binom(s[u], u + 1);
+    const double *invw = inv + w * NT;
+    DF ai[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) ai[q] = df_of(invw[q]);
+    auto AI = [&](int r, int c) { return r >= c ? ai[r * (r + 1) / 2 + c] : ai[c * (c + 1) / 2 + r]; };
+    int gr[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) gr[u] = u < DP ? s[u] : s[u - DP] + M;
+    uint64_t baseT = o.off[D];
+#pragma unroll
+    for (int u = 0; u < DP; ++u) baseT += binom(s[u], u + 2);
+    const float4 *A4 = reinterpret_cast<const float4 *>(Af);
+    double sumC = 0.0;
+    DFAcc acc[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) acc[q] = DFAcc{0.f, 0.f};
+    // The lanes of a warp share s0 (and so their trip count). Each starts its walk
+    // over the leaves at its own j, so that their atomic adds to row s0 and to the
+    // j diagonal block go to different addresses instead of one.
+    int j = (int)(threadIdx.x & 31u) % s0;
+    for (int t = 0; t < s0; ++t, j = (j + 1 == s0) ? 0 : j + 1) {
+        const double g = gp0[baseT + j];
+        if (g == 0.0) continue;
+        const double C64 = -0.25 * g * p0[baseT + j];
+        const DF C = df_of(C64);
+        DF b[N][2];
+#pragma unroll
+        for (int u = 0; u < DP; ++u) {
+            const size_t bi = 2 * ((size_t)s[u] * M + j);
+            const float4 bh = A4[bi], bl = A4[bi + 1];
+            b[u][0] = DF{bh.x, bl.x};
+            b[u][1] = DF{bh.y, bl.y};
+            b[u + DP][0] = DF{bh.z, bl.z};
+            b[u + DP][1] = DF{bh.w, bl.w};
+        }
+        DF uu[N][2];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            DFAcc x0{0.f, 0.f}, x1{0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                dfa_fma(x0, AI(r, c), b[c][0]);
+                dfa_fma(x1, AI(r, c), b[c][1]);
+            }
+            uu[r][0] = dfa_val(x0);
+            uu[r][1] = dfa_val(x1);
+        }
+        const size_t di = 2 * ((size_t)j * M + j);
+        const float4 dh = A4[di], dl = A4[di + 1];
+        DFAcc S00{dh.x, dl.x}, S11{dh.w, dl.w};
+        // the symmetric part of the off-diagonal pair, (a01 + a10) / 2, as for blk_sym
+        DFAcc S01{dh.y, dl.y};
+        dfa_fma(S01, DF{dh.z, dl.z}, DF{1.f, 0.f});
+        S01.s *= 0.5f;
+        S01.t *= 0.5f;
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            dfa_fma(S00, df_neg(b[r][0]), uu[r][0]);
+            dfa_fma(S01, df_neg(b[r][0]), uu[r][1]);
+            dfa_fma(S11, df_neg(b[r][1]), uu[r][1]);
+        }
+        const DF s00 = dfa_val(S00), s01 = dfa_val(S01), s11 = dfa_val(S11);
+        DFAcc dt{0.f, 0.f};
+        dfa_fma(dt, s00, s11);
+        dfa_fma(dt, df_neg(s01), s01);
+        const DF det = dfa_val(dt);
+        if (!(det.h > 0.f) || !(s00.h > 0.f)) {
+            flag_status(status, ST_NOT_POSDEF);
+            continue;
+        }
+        sumC += C64;
+        const DF Cd = df_div(C, det);
+        const DF i00 = df_prod(s11, Cd), i01 = df_neg(df_prod(s01, Cd)), i11 = df_prod(s00, Cd);  // C S^{-1}
+        DF cv[N][2];  // C v = u (C S^{-1})
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            DFAcc c0{0.f, 0.f}, c1{0.f, 0.f};
+            dfa_fma(c0, uu[r][0], i00);
+            dfa_fma(c0, uu[r][1], i01);
+            dfa_fma(c1, uu[r][0], i01);
+            dfa_fma(c1, uu[r][1], i11);
+            cv[r][0] = dfa_val(c0);
+            cv[r][1] = dfa_val(c1);
+        }
+        int q = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c, ++q) {
+                dfa_fma(acc[q], cv[r][0], uu[c][0]);
+                dfa_fma(acc[q], cv[r][1], uu[c][1]);
+            }
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            const int g0 = gr[r];
+            atomicAdd(gV + (size_t)g0 * n2 + j, -df_to_double(cv[r][0]));  // g0 > j
+            const int jm = j + M;
+            const double v1 = -df_to_double(cv[r][1]);
+            if (g0 >= jm) atomicAdd(gV + (size_t)g0 * n2 + jm, v1);
+            else atomicAdd(gV + (size_t)jm * n2 + g0, v1);
+        }
+        atomicAdd(gV + (size_t)j * n2 + j, df_to_double(i00));
+        atomicAdd(gV + (size_t)(j + M) * n2 + j, df_to_double(i01));
+        atomicAdd(gV + (size_t)(j + M) * n2 + j + M, df_to_double(i11));
+    }
+    if (sumC != 0.0) {
+        int q = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+#pragma unroll
+            for (int c = 0; c <= r; ++c, ++q) {
+                const double v = fma(sumC, invw[q], df_to_double(dfa_val(acc[q])));
+                const int hi2 = gr[r] > gr[c] ? gr[r] : gr[c], lo2 = gr[r] > gr[c] ? gr[c] : gr[r];
+                atomicAdd(gV + (size_t)hi2 * n2 + lo2, v);
+            }
+    }
+}
+
 // Mirror the accumulated lower triangle of dV into the upper triangle.
 __global__ void mirror_kernel(int n2, double *__restrict__ gV) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -562,10 +752,12 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
         if (a.ev) cudaEventRecord(a.ev[i], st);
     };
     mark(0);
-    // 1. P0 table of every order (forward kernels, FP64)
+    // 1. P0 table of every order (forward kernels, refined FP32: relative error
+    //    about 1e-13, well inside what the double-float scatter keeps; its packing
+    //    also leaves the float-pair copy of A that the scatter reads)
     FwdArgs f = a.fwd;
     f.mode = MODE_P0;
-    f.precision = GBS_FP64;
+    f.precision = GBS_FP32_REFINED;
     f.p0 = f.out = a.p0;
     if ((e = launch_forward(f, st)) != cudaSuccess) return e;
     mark(1);
@@ -616,7 +808,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t st) {
         ainv_kernel<DD - 1><<<gi, BWD_THREADS, 0, st>>>(M, f.A, a.inv, f.status);                          \
         if ((e = cudaGetLastError()) != cudaSuccess) return e;                                             \
         if (DD <= 3) gv2_kernel<DD - 1, 4><<<gc, 128, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status); \
-        else if (gw) gv2_kernel<DD - 1, 0><<<gw, 128, 0, st>>>(M, o, f.A, a.p0, a.gp0, a.inv, a.gV, f.status); \
+        else if (gw) gv2df_kernel<DD - 1><<<gw, 128, 0, st>>>(M, o, f.Af, a.p0, a.gp0, a.inv, a.gV, f.status); \
         break;
             GV2_CASE(2)
             GV2_CASE(3)
