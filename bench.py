@@ -87,7 +87,8 @@ def parse():
                    help="default run: skip the secondary workloads (batch, fitting, displaced, sampler)")
     p.add_argument("--batch", type=int, default=8192, help="samples per step (sample144)")
     p.add_argument("--cpu-sample", type=int, default=0, help="subsets per CPU-baseline sample (0 = auto)")
-    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "disp144", "sample144"],
+    p.add_argument("--workload", choices=["m144k5", "m100k5", "batch256", "fit100", "adjoint100", "disp144",
+                                          "sample144"],
                    default="m144k5",
                    help="m100k5: smaller case of the same kernels for profiling; batch256: the 256-instance "
                         "ragged batch; fit100: forward + adjoint of the M=100 kmax=4 fitting loss")
@@ -408,10 +409,16 @@ def run_batch(precision, steps, warmup, autotune, peaks, sms, sm_mhz):
     return rec
 
 
-# FP64 flops (FMA = 2) of the adjoint phases at M=100, kmax=4, from the ncu SASS
-# counters of one gbs_cumulants_backward call (sum over the phase's kernels);
-# None = not captured.
-FIT_PHASE_FP64_FLOPS = {"p0_recompute": None, "h_table": 2293700, "gp0_gather": None, "gv_scatter": None}
+# Executed instructions of the adjoint phases at M=100, kmax=4, from the ncu SASS
+# counters of one gbs_cumulants_backward call (sum over the phase's kernels):
+# FP64 flops (FMA = 2), FP64-pipe instructions, FP32 instructions; None = not
+# captured (or stale after a kernel change).
+FIT_PHASE_COUNTS = {
+    "p0_recompute": {"fp64_flops": 34599015, "fp64_instr": 22408520, "fp32_instr": 1701487776},
+    "h_table": {"fp64_flops": 2293700, "fp64_instr": 1146850, "fp32_instr": 3758700},
+    "gp0_gather": {"fp64_flops": 118296845, "fp64_instr": 62419595, "fp32_instr": 9289756},
+    "gv_scatter": {"fp64_flops": 220049841, "fp64_instr": 179690437, "fp32_instr": 8485702640},
+}
 
 
 def run_fit(steps, warmup, peaks):
@@ -465,10 +472,19 @@ def run_fit(steps, warmup, peaks):
     phases /= 3
     names = ["p0_recompute", "h_table", "gp0_gather", "gv_scatter"]
     roof = {"phases_ms": dict(zip(names, phases.tolist()))}
-    if FIT_PHASE_FP64_FLOPS:
-        roof["fp64"] = {k: {"achieved_tflops": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / 1e12,
-                            "frac": FIT_PHASE_FP64_FLOPS[k] / (t * 1e-3) / peaks["fp64_flops"]}
-                        for k, t in zip(names, phases) if FIT_PHASE_FP64_FLOPS.get(k) and t > 0}
+    # per phase: FP64 flops against the measured FP64 peak, and the FP64 / FP32
+    # pipes' instruction rates against their measured peaks (FMA instructions/s)
+    roof["pipes"] = {}
+    for k, t in zip(names, phases):
+        c = FIT_PHASE_COUNTS.get(k)
+        if not c or t <= 0:
+            continue
+        sec = t * 1e-3
+        roof["pipes"][k] = {
+            "fp64_achieved_tflops": c["fp64_flops"] / sec / 1e12,
+            "fp64_frac": c["fp64_flops"] / sec / peaks["fp64_flops"],
+            "fp64_pipe_frac": c["fp64_instr"] / sec / (peaks["fp64_flops"] / 2),
+            "fp32_pipe_frac": c["fp32_instr"] / sec / (peaks["fp32_flops"] / 2)}
     N = gbs.table_size(M, K)
     return {"metric": "fitting step (forward + adjoint), M=100 kmax=4", "value": N / (ms * 1e-3),
             "unit": "subsets/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
@@ -634,8 +650,44 @@ def run_sampler(args, steps, warmup, batch, hbm, with_fp64=True, with_e2e=True):
     return rec
 
 
+def run_adjoint(steps, warmup):
+    """gbs_cumulants_backward alone on the M=100, kmax=4 fitting instance (random
+    dL/dkt): CUDA-event time per call, then one more call between
+    cudaProfilerStart and cudaProfilerStop, so that a profiler started with
+    --profile-from-start off sees exactly one adjoint's kernels."""
+    import torch
+    import synthetic
+    import paper_2511_14923_gb300 as gbs
+    inst = synthetic.config(3)
+    M, K = inst.M, inst.kmax
+    V = torch.from_numpy(inst.V).cuda()
+    gbs.autotune(V, K, "fp32r")  # untimed: the schedule of the adjoint's P0 pass
+    g = torch.randn(gbs.table_size(M, K), dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(7))
+    ws = torch.empty(int(gbs.lib().gbs_backward_workspace_bytes(M, K)), dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        gbs.cumulants_backward(V, K, g, workspace=ws)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, e in ev:
+        a.record()
+        gbs.cumulants_backward(V, K, g, workspace=ws, check=False)
+        e.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in ev) / steps
+    gbs.cumulants_backward(V, K, g, workspace=ws, check=True)  # raises on a device error
+    torch.cuda.profiler.start()
+    gbs.cumulants_backward(V, K, g, workspace=ws, check=False)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    return {"metric": "adjoint (gbs_cumulants_backward), M=100 kmax=4", "value": ms, "unit": "ms",
+            "steps": steps, "warmup": warmup, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "M=100 kmax=4 fitting instance, random dL/dkt (seed 7)",
+                       "subsets": gbs.table_size(M, K)}}
+
+
 def standalone(args, which):
-    """--workload batch256 | fit100 | disp144 | sample144: that workload alone."""
+    """--workload batch256 | fit100 | adjoint100 | disp144 | sample144: that workload alone."""
     import torch
     import paper_2511_14923_gb300 as gbs
     if which == "sample144":
@@ -651,6 +703,8 @@ def standalone(args, which):
         rec = run_batch(args.precision, args.steps, args.warmup, not args.no_autotune, peaks, sms, mhz)
     elif which == "fit100":
         rec = run_fit(args.steps, args.warmup, peaks)
+    elif which == "adjoint100":
+        rec = run_adjoint(args.steps, args.warmup)
     elif which == "disp144":
         rec = run_displaced(args.steps, args.warmup, peaks, sms, mhz)
     else:
@@ -666,7 +720,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload in ("batch256", "sample144", "disp144", "fit100"):
+    if args.workload in ("batch256", "sample144", "disp144", "fit100", "adjoint100"):
         standalone(args, args.workload)
         return
     import torch
@@ -753,19 +807,27 @@ def main():
                     done[b].record(xs)
 
         def timed(fn):
+            # wall clock around n_e2e steps, synchronised on both sides; three
+            # repetitions, the median reported (the overlap of the 3.99 GB copy to
+            # host memory with the next step's kernels varies between runs)
             fn(2)
             torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            fn(n_e2e)
-            torch.cuda.synchronize(dev)
-            return (time.perf_counter() - t0) * 1e3 / n_e2e
+            reps = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                fn(n_e2e)
+                torch.cuda.synchronize(dev)
+                reps.append((time.perf_counter() - t0) * 1e3 / n_e2e)
+            return statistics.median(reps), reps
 
-        seq_ms = timed(seq_steps)
-        pipe_ms = timed(pipe_steps)
+        seq_ms, seq_reps = timed(seq_steps)
+        pipe_ms, pipe_reps = timed(pipe_steps)
         e2e = {"value": N * world / (pipe_ms * 1e-3), "unit": "subsets/s", "ms_per_step": pipe_ms,
                "h2d_bytes_per_step": int(hV.numel() * 8), "d2h_bytes_per_step": int(N * 8),
                "pipelined": "table of step k copied back while step k+1 computes (two device buffers)",
-               "sequential_ms_per_step": seq_ms, "sequential_value": N * world / (seq_ms * 1e-3)}
+               "repetitions_ms": pipe_reps, "steps_per_repetition": n_e2e,
+               "sequential_ms_per_step": seq_ms, "sequential_value": N * world / (seq_ms * 1e-3),
+               "sequential_repetitions_ms": seq_reps}
         del hout, outs, dV
     del out, wss, flush
     torch.cuda.empty_cache()
