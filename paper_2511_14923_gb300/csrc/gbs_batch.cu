@@ -314,7 +314,7 @@ KernelInfo kinfo() {
 }
 
 bool variant_ok(int precision, int variant, int maxM) {
-    if (variant < 0 || variant >= kNumVariants || variant_clustered(variant)) return false;
+    if (variant < 0 || variant >= kNumVariants || variant_clustered(variant) || variant == 9) return false;
     if (precision == 0 && variant >= 2) return false;
     if ((variant == 1 || variant == 3) && maxM > kVariant1MaxM) return false;
     if (variant == 5 && maxM > kVariant5MaxM) return false;

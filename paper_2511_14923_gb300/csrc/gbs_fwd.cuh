@@ -39,7 +39,7 @@ struct FwdArgs {
     // memory batch, CTA shape (0: 512 threads x 1 per SM; 1: 256 x 2; refined path
     // only: 2: 640 x 1, 3: 256 x 3, 4: 768 x 1 with a 2048-entry x area, 5: 384 x 2
     // with a 960-entry x area, 6: 256 x 4 with a 384-entry x area, 7: 6 in clusters
-    // of 4, 8: 3 in clusters of 3)
+    // of 4, 8: 3 in clusters of 3, 9: 6 without Schur-complement slots)
     int grain, ccap, variant;
 };
 
@@ -68,9 +68,15 @@ constexpr int kVariant5MaxM = kPairXC + 1;
 // x-entries per batch of the 256-thread x 4 refined variant, and its largest M.
 constexpr int kQuadXC = 384;
 constexpr int kVariant6MaxM = kQuadXC + 1;
+// The slot-free 256-thread x 4 refined variant: children per batch it has room
+// for, and the elimination rows Y(x), x < c4 <= M - 2, it keeps in shared memory.
+constexpr int kNoSlotCC = 24;
+constexpr int kNoSlotYC = 160;
+constexpr int kVariant9MaxM = kNoSlotYC + 1;  // order 4 reaches c4 = M - 1
 // Number of CTA shapes (variants 0..kNumVariants-1); 7 and 8 are the 256 x 4 and
-// 256 x 3 shapes in thread-block clusters of 4 and 3 CTAs sharing one slot.
-constexpr int kNumVariants = 9;
+// 256 x 3 shapes in thread-block clusters of 4 and 3 CTAs sharing one slot, 9 the
+// 256 x 4 shape without slots.
+constexpr int kNumVariants = 10;
 // Whether a variant runs in clusters (the batched kernel has no clustered form).
 inline bool variant_clustered(int v) { return v == 7 || v == 8; }
 

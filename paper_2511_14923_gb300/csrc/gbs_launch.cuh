@@ -27,9 +27,9 @@ __global__ void order3_kernel(FwdArgs a, bool write_p0, uint64_t first, uint64_t
     if (i < count) order3_entry<MODE, DISP>(a, first + i, write_p0);
 }
 
-template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP, int CC = CCAP, int YC = 0>
 __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t target, bool write_p0) {
-    using SH = TreeShared<D, XC, DISP>;
+    using SH = TreeShared<D, XC, DISP, CC, YC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = *reinterpret_cast<SH *>(smem_raw);
     const int tid = threadIdx.x;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NT, MINB) tree_kernel(FwdArgs a, uint64_t targ
         const uint32_t rr = item - sh.c4pref[lo];
         const int u = (int)(rr / nc), s = (int)(rr % nc);
         const int c5 = (D == 5) ? c5_first(c4, tlo) + u : M;
-        tree_item<D, MODE, PREC, NT, XC, DISP>(a, sh, slot, c4, c5, s, nc, write_p0, a.ccap);
+        tree_item<D, MODE, PREC, NT, XC, DISP, false, CC, YC>(a, sh, slot, c4, c5, s, nc, write_p0, a.ccap);
     }
 }
 
@@ -190,15 +190,15 @@ static cudaError_t launch_tree_cl(const FwdArgs &a, bool write_p0, cudaStream_t 
     return cudaGetLastError();
 }
 
-template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP>
+template <int D, int MODE, int PREC, int NT, int XC, int MINB, bool DISP, int CC = CCAP, int YC = 0>
 static cudaError_t launch_tree_v(const FwdArgs &a, bool write_p0, cudaStream_t st) {
     const int M = a.M;
     const bool ranged = a.top != nullptr && D == a.kmax;
     const int tlo = ranged ? a.c_lo : 0, thi = ranged ? a.c_hi : M;
     const uint64_t leaves = binom(thi, D) - binom(tlo, D);
     if (leaves == 0) return cudaSuccess;
-    const size_t smem = sizeof(TreeShared<D, XC, DISP>);
-    auto fn = tree_kernel<D, MODE, PREC, NT, XC, MINB, DISP>;
+    const size_t smem = sizeof(TreeShared<D, XC, DISP, CC, YC>);
+    auto fn = tree_kernel<D, MODE, PREC, NT, XC, MINB, DISP, CC, YC>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -246,6 +246,9 @@ static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t 
                 return launch_tree_cl<D, MODE, PREC, 256, kQuadXC, 4, 4>(a, write_p0, st);
             if (a.variant == 8 && a.M <= kVariant1MaxM)
                 return launch_tree_cl<D, MODE, PREC, 256, 576, 3, 3>(a, write_p0, st);
+            // 256 x 4 without slots: Schur-complement blocks formed from Y where used
+            if (a.variant == 9 && a.M <= kVariant9MaxM)
+                return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false, kNoSlotCC, kNoSlotYC>(a, write_p0, st);
         }
         return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP, 1, false>(a, write_p0, st);
     }

@@ -171,9 +171,12 @@ __device__ __forceinline__ void ord3(int x, int y, int z, int &p, int &q, int &r
     p = x; q = y; r = z;
 }
 
-// Pair rank -> (hi, lo), hi > lo >= 0 (colex: rank = C(hi, 2) + lo).
+// Pair rank -> (hi, lo), hi > lo >= 0 (colex: rank = C(hi, 2) + lo). The root
+// estimate is taken in FP32 (GB300's FP64 pipe is narrow and every lane of the
+// table kernels decodes its pair) and corrected exactly by the loops.
 __device__ __forceinline__ void pair_of(uint64_t r, int &hi, int &lo) {
-    int c = (int)(0.5 * (1.0 + sqrt(1.0 + 8.0 * (double)r)));
+    int c = (int)(0.5f * (1.f + sqrtf(1.f + 8.f * (float)r)));
+    if (c < 1) c = 1;
     while (cb(c, 2) > r) --c;
     while (cb(c + 1, 2) <= r) ++c;
     hi = c;
@@ -1265,15 +1268,22 @@ __global__ void kscale_kernel(const double *__restrict__ kap, int M, int d, uint
     int c[6];
     colex_unrank(r0, d, c);
     c[d] = M;  // sentinel
-    for (uint64_t r = r0; r < r1; ++r) {
+    // product of the scales of c[1..d-1], formed again only when one of them moves
+    // (GB300's FP64 pipe is narrow: most successors move c[0] alone)
+    auto upper = [&]() {
         double f = 1.0;
-        for (int i = 0; i < d; ++i) f *= (double)hs[c[i] + 1];
-        out[off + r] = (R)(kap[off + r] * f);
+        for (int i = d - 1; i >= 1; --i) f *= (double)hs[c[i] + 1];
+        return f;
+    };
+    double fu = upper();
+    for (uint64_t r = r0; r < r1; ++r) {
+        out[off + r] = (R)(kap[off + r] * (fu * (double)hs[c[0] + 1]));
         // successor: the first element that can move up moves up, the ones below reset
         int i = 0;
         while (i < d - 1 && c[i] + 1 == c[i + 1]) ++i;
         ++c[i];
         for (int j = 0; j < i; ++j) c[j] = j;
+        if (i > 0 && r + 1 < r1) fu = upper();
     }
 }
 

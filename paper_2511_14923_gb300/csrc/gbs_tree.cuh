@@ -255,7 +255,11 @@ __device__ __forceinline__ void order3_entry(const FwdArgs &a, uint64_t r, bool 
 
 // ---------------------------------------------------------------- tree kernel
 
-template <int D, int XC = XCAP, bool DISP = false>
+// CC: children per batch it has room for. YC > 0: the slot-free form of the
+// refined path, which keeps the item's elimination rows Y(x) (x < c4 <= YC) in
+// yq for the whole item and forms every Schur-complement block it needs from
+// them instead of reading a slot.
+template <int D, int XC = XCAP, bool DISP = false, int CC = CCAP, int YC = 0>
 struct TreeShared {
     static constexpr int NP = D - 2;       // |P|
     static constexpr int NQ = 1 << NP;     // subsets of P
@@ -266,15 +270,15 @@ struct TreeShared {
     // uniform pivots of the item's U (and, displaced, their whitened half-means)
     double upiv[DISP ? 10 : 8];
     // children of the current batch
-    int c3[CCAP];
-    int xoff[CCAP + 1];
-    uint32_t lpref[CCAP + 1];
-    uint64_t baseJ[CCAP][NQ];
-    uint64_t baseT[CCAP][NQ];
-    double p0R[CCAP][NQ];
-    double m3[CCAP][3];
-    float m3f[CCAP][6];  // refined path: m3 as float pairs (h, l) x 3
-    double g3[DISP ? CCAP : 1][2];  // displaced: whitened half-mean of each child's c3 pivot
+    int c3[CC];
+    int xoff[CC + 1];
+    uint32_t lpref[CC + 1];
+    uint64_t baseJ[CC][NQ];
+    uint64_t baseT[CC][NQ];
+    double p0R[CC][NQ];
+    double m3[CC][3];
+    float m3f[CC][6];  // refined path: m3 as float pairs (h, l) x 3
+    double g3[DISP ? CC : 1][2];  // displaced: whitened half-mean of each child's c3 pivot
     // Per x-entry data, structure of arrays. FP64 path (10 double rows):
     // z(x) = m3 * S_U[c3, x] (rows 0-3), d(x) = S_U[x,x] - z^T z (rows 4-6),
     // inverse c2-pivot factor m2(x) (rows 7-9). Refined-FP32 path (6 float4
@@ -290,6 +294,9 @@ struct TreeShared {
     static constexpr int XROWS = DISP ? 14 : 10;
     static constexpr int XBYTES = (6 * 16 > XROWS * 8 ? 6 * 16 : XROWS * 8) * XC;
     alignas(16) unsigned char xraw[XBYTES];
+    // slot-free form: Y(x) as 16 floats (hi, lo of y5 00 01 10 11, then of y4) in
+    // four float4 rows, row r holding floats 4r..4r+3 of every x
+    alignas(16) float4 yq[YC > 0 ? 4 : 1][YC > 0 ? YC : 1];
     __device__ double (*xe())[XC] { return reinterpret_cast<double(*)[XC]>(xraw); }
     __device__ float (*xf())[XC] { return reinterpret_cast<float(*)[XC]>(xraw); }
     __device__ float4 (*xq())[XC] { return reinterpret_cast<float4(*)[XC]>(xraw); }
@@ -340,6 +347,36 @@ __device__ __forceinline__ void slot_store_diag(double *sdiag, int x, const Sym 
     float4 *f = reinterpret_cast<float4 *>(sdiag) + 2 * (size_t)x;
     f[0] = h;
     f[1] = l;
+}
+
+// Schur-complement block S_U[x][y] (x >= y) of the refined path formed from A's
+// float-pair block and the rows Y(x), Y(y) of the eliminated modes U:
+// b_uv -= sum_k y(x)_ku y(y)_kv over the pivot rows k of c5 (D = 5) and c4, in
+// float pairs on the FP32 pipe. The same operations in the same order as the
+// slot build, so both forms give the same bits.
+template <int D, int YC>
+__device__ __forceinline__ void su_block(const float *__restrict__ Af, int M, const float4 (*yq)[YC], int x, int y,
+                                         DF (&b)[4]) {
+    const float4 a0 = reinterpret_cast<const float4 *>(Af)[2 * ((size_t)x * M + y)];
+    const float4 a1 = reinterpret_cast<const float4 *>(Af)[2 * ((size_t)x * M + y) + 1];
+    b[0] = DF{a0.x, a1.x};
+    b[1] = DF{a0.y, a1.y};
+    b[2] = DF{a0.z, a1.z};
+    b[3] = DF{a0.w, a1.w};
+    // one pivot row k of one eliminated mode at a time: x's elements (k, 0), (k, 1)
+    // and y's in one float4 each; every element still takes its four updates in
+    // the build's order (c5 row 0, c5 row 1, c4 row 0, c4 row 1)
+#pragma unroll
+    for (int blk = (D == 5 ? 0 : 1); blk < 2; ++blk)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float4 xr = yq[2 * blk + k][x], yr = yq[2 * blk + k][y];
+            const DF x0{xr.x, xr.y}, x1{xr.z, xr.w}, y0{yr.x, yr.y}, y1{yr.z, yr.w};
+            b[0] = df_sub_mul(b[0], x0, y0);
+            b[1] = df_sub_mul(b[1], x0, y1);
+            b[2] = df_sub_mul(b[2], x1, y0);
+            b[3] = df_sub_mul(b[3], x1, y1);
+        }
 }
 
 // Number of stride classes the children c3 in [2, c4) of one U are split into.
@@ -407,13 +444,23 @@ __device__ __forceinline__ void store_entry(const FwdArgs &a, int d, uint64_t id
 // barrier (release / acquire, so the other CTAs' global writes are visible)
 // replaces the block barrier after the build; the caller passes s = part,
 // nc = nparts, so each CTA then takes one stride class of the children.
-template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false, bool CL = false>
-__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DISP> &sh, double *const slot,
+//
+// YC > 0 (refined path only): no slot. Y(x) stays in shared memory for the
+// whole item and each Schur-complement block is formed where it is used
+// (su_block): the c3 pivots, z(x) and d(x) of the batch setup, and one block per
+// leaf pair and batch. That trades a few FP32 operations per leaf for the
+// slot's DRAM writes and re-reads.
+template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false, bool CL = false,
+          int CC = CCAP, int YC = 0>
+__device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DISP, CC, YC> &sh, double *const slot,
                                           const int c4, const int c5, const int s, const int nc, const bool write_p0,
-                                          const int ccap = CCAP, const int part = 0, const int nparts = 1) {
+                                          const int ccap_in = CCAP, const int part = 0, const int nparts = 1) {
     static_assert(!DISP || PREC == 0, "displaced states run in FP64");
     static_assert(!(DISP && CL), "displaced states run without clusters");
-    using SH = TreeShared<D, XC, DISP>;
+    constexpr bool NOSLOT = YC > 0;
+    static_assert(!NOSLOT || (PREC == 1 && !CL), "the slot-free form is the refined path's, without clusters");
+    const int ccap = ccap_in < CC ? ccap_in : CC;
+    using SH = TreeShared<D, XC, DISP, CC, YC>;
     constexpr int NP = SH::NP;
     constexpr int NQ = SH::NQ;
     constexpr int PALL = NQ - 1;
@@ -426,6 +473,12 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
     double *const rU = sdiag + 4 * (size_t)M;  // displaced: reduced half-means, 2 per mode
     const double *__restrict__ A = a.A;
 
+    if constexpr (NOSLOT) {
+        if (c4 > YC) {  // Y rows beyond the shared area (the launcher bounds M): reject, block-uniformly
+            if (tid == 0) flag_status(a.status, ST_BAD_INDEX);
+            return;
+        }
+    }
     // ---- Schur complement of A after eliminating U, modes < c4 -> slot
     // uniform pivots: m5 = chol(A[c5,c5])^{-1}, y5(c4), m4 = chol(Pi4)^{-1}
     if (tid == 0) {
@@ -479,7 +532,13 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                 rU[2 * x + 1] = r.v1;
             }
             const double v[8] = {y5.a00, y5.a01, y5.a10, y5.a11, y4.a00, y4.a01, y4.a10, y4.a11};
-            if (PREC == 0) {
+            if constexpr (NOSLOT) {
+                float f[16];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) split_df(v[k], f[2 * k], f[2 * k + 1]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sh.yq[r][x] = make_float4(f[4 * r], f[4 * r + 1], f[4 * r + 2], f[4 * r + 3]);
+            } else if (PREC == 0) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) Y[8 * x + k] = v[k];
             } else {
@@ -488,6 +547,8 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
             }
         }
         __syncthreads();
+        // the slot build (the slot-free form has nothing more to do: Y is in place)
+        if constexpr (!NOSLOT) {
         const uint32_t npairs = (uint32_t)binom2(c4);
         for (uint32_t qi = (uint32_t)(part * NT + tid); qi < npairs + (uint32_t)c4; qi += (uint32_t)(nparts * NT)) {
             int x, y;
@@ -534,6 +595,7 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
         }
         if constexpr (CL) cooperative_groups::this_cluster().sync();
         else __syncthreads();
+        }
     }
 
     // ---- children c3 = c4-1-s, c4-1-s-nc, ... >= 2, processed in batches
@@ -579,7 +641,14 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
             for (int q = 1; q < NQ; ++q) sh.p0R[b][q] = a.p0[idxQ[q]];
             bool ok;
             double dd;
-            const Sym p3 = slot_diag_f64<PREC>(sdiag, c3);
+            Sym p3;
+            if constexpr (NOSLOT) {
+                DF b[4];
+                su_block<D, YC>(a.Af, M, sh.yq, c3, c3, b);
+                p3 = Sym{join_df(b[0].h, b[0].l), join_df(b[1].h, b[1].l), join_df(b[3].h, b[3].l)};
+            } else {
+                p3 = slot_diag_f64<PREC>(sdiag, c3);
+            }
             const LInv m3 = chol2_inv(p3, ok, dd);
             if (!ok) flag_status(a.status, ST_NOT_POSDEF);
             sh.m3[b][0] = m3.m00; sh.m3[b][1] = m3.m10; sh.m3[b][2] = m3.m11;
@@ -630,16 +699,26 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
                 }
             } else {
                 // z(x) = m3 S_U[c3, x] and d(x) = S_U[x, x] - z^T z in float pairs (FP32 pipe)
-                const float *fs = reinterpret_cast<const float *>(slot) + 8 * (binom2(c3) + x);
-                const float *fd = reinterpret_cast<const float *>(sdiag) + 8 * x;
-                const DF S00{fs[0], fs[4]}, S01{fs[1], fs[5]}, S10{fs[2], fs[6]}, S11{fs[3], fs[7]};
+                DF S00, S01, S10, S11, D00, D01, D11;
+                if constexpr (NOSLOT) {
+                    DF b[4];
+                    su_block<D, YC>(a.Af, M, sh.yq, c3, x, b);
+                    S00 = b[0]; S01 = b[1]; S10 = b[2]; S11 = b[3];
+                    su_block<D, YC>(a.Af, M, sh.yq, x, x, b);
+                    D00 = b[0]; D01 = b[1]; D11 = b[3];
+                } else {
+                    const float *fs = reinterpret_cast<const float *>(slot) + 8 * (binom2(c3) + x);
+                    const float *fd = reinterpret_cast<const float *>(sdiag) + 8 * x;
+                    S00 = DF{fs[0], fs[4]}; S01 = DF{fs[1], fs[5]}; S10 = DF{fs[2], fs[6]}; S11 = DF{fs[3], fs[7]};
+                    D00 = DF{fd[0], fd[3]}; D01 = DF{fd[1], fd[4]}; D11 = DF{fd[2], fd[5]};
+                }
                 const DF m00{sh.m3f[b][0], sh.m3f[b][1]}, m10{sh.m3f[b][2], sh.m3f[b][3]}, m11{sh.m3f[b][4], sh.m3f[b][5]};
                 const DF z00 = df_mul(m00, S00), z01 = df_mul(m00, S01);
                 const DF z10 = df_add_mul(df_mul(m10, S00), m11, S10);
                 const DF z11 = df_add_mul(df_mul(m10, S01), m11, S11);
-                const DF d00 = df_sub_mul(df_sub_mul(DF{fd[0], fd[3]}, z00, z00), z10, z10);
-                const DF d01 = df_sub_mul(df_sub_mul(DF{fd[1], fd[4]}, z00, z01), z10, z11);
-                const DF d11 = df_sub_mul(df_sub_mul(DF{fd[2], fd[5]}, z01, z01), z11, z11);
+                const DF d00 = df_sub_mul(df_sub_mul(D00, z00, z00), z10, z10);
+                const DF d01 = df_sub_mul(df_sub_mul(D01, z00, z01), z10, z11);
+                const DF d11 = df_sub_mul(df_sub_mul(D11, z01, z01), z11, z11);
                 xq[0][e] = make_float4(z00.h, z01.h, z10.h, z11.h);
                 xq[1][e] = make_float4(z00.l, z01.l, z10.l, z11.l);
                 xq[2][e] = make_float4(d00.h, d01.h, d11.h, d00.l);
@@ -682,6 +761,10 @@ __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DI
             DFBlk Sdf{};
             if constexpr (PREC == 0) {
                 S64 = load_blk(slot + 4 * (size_t)t);
+            } else if constexpr (NOSLOT) {
+                DF b[4];
+                su_block<D, YC>(a.Af, M, sh.yq, c2, j, b);
+                Sdf = DFBlk{b[0].h, b[1].h, b[2].h, b[3].h, b[0].l, b[1].l, b[2].l, b[3].l};
             } else {
                 const float4 *fs = reinterpret_cast<const float4 *>(slot) + 2 * (size_t)t;
                 const float4 sh4 = fs[0], sl4 = fs[1];

@@ -7,7 +7,8 @@
 //   variant CTA shape: 512 threads x 1 per SM; 256 x 2 per SM (M <= 577); and for
 //           the refined path 640 x 1, 256 x 3 (M <= 577), 768 x 1 with room
 //           for more children per batch, 384 x 2 (M <= 961), 256 x 4 (M <= 385),
-//           or 256 x 4 / 256 x 3 in thread-block clusters sharing one slot.
+//           256 x 4 / 256 x 3 in thread-block clusters sharing one slot, or
+//           256 x 4 without slots (M <= 162).
 // Results live in a process-wide table consulted by every forward call; if the
 // environment variable GBS_AUTOTUNE_CACHE names a file, the table is loaded from
 // it on first use and rewritten after each tuning run (a JSON array of objects).
@@ -206,8 +207,9 @@ int autotune(FwdArgs a, cudaStream_t st, TreeCfg &best, float &best_ms, int &tri
         if (variant == 5 && a.M > kVariant5MaxM) continue;
         if ((variant == 6 || variant == 7) && a.M > kVariant6MaxM) continue;
         if (variant == 8 && a.M > kVariant1MaxM) continue;
+        if (variant == 9 && a.M > kVariant9MaxM) continue;
         for (int grain : {1, 2, 4, 8})
-            for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, ccap, variant});
+            for (int ccap : {16, 64}) cand.push_back(TreeCfg{grain, variant == 9 && ccap > kNoSlotCC ? kNoSlotCC : ccap, variant});
     }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return GBS_ERR_CUDA;

@@ -51,7 +51,7 @@ def test_json_cache_round_trip(tmp_path):
     entries = json.loads(cache.read_text())
     assert any(e["M"] == 30 and e["kmax"] == 5 and e["precision"] == 1 for e in entries)
     e = [e for e in entries if e["M"] == 30][0]
-    assert e["grain"] in (1, 2, 4, 8) and e["ccap"] in (16, 64) and e["variant"] in range(9)
+    assert e["grain"] in (1, 2, 4, 8) and e["ccap"] in (16, 24, 64) and e["variant"] in range(10)
     # a second process loads the file and reuses it (and still computes the same table)
     out2 = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT)], env=env, capture_output=True, text=True)
     assert out2.returncode == 0, out2.stderr
@@ -78,7 +78,7 @@ print(hashlib.sha256(t.cpu().numpy().tobytes()).hexdigest())
 """
 
 
-@pytest.mark.parametrize("prec,variants", [("fp64", (0, 1)), ("fp32r", (0, 1, 2, 3, 4, 5, 6, 7, 8))])
+@pytest.mark.parametrize("prec,variants", [("fp64", (0, 1)), ("fp32r", (0, 1, 2, 3, 4, 5, 6, 7, 8, 9))])
 def test_every_cta_shape_gives_identical_table(tmp_path, prec, variants):
     """Each CTA shape, pinned through the cache file, fills the same table bit for bit."""
     digests = set()
