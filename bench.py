@@ -61,10 +61,12 @@ OPS_PER_ENTRY = {
     ("fp64", 4): {"dfma": 33.458, "dadd": 0.013, "dmul": 8.375, "fp32": 13.474},
 }
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# order-5 kernel at M=144 under the same pinned schedules (ncu, tree kernels
-# only, mean of the warm-up and timed launches); None once the kernel has
-# changed since the capture.
-TRAFFIC_BYTES = {"fp32r": 5.7475e9 + 4.3202e9, "fp64": 3.4121e9 + 4.2817e9}
+# order-5 kernel at M=144, by precision and CTA shape (gbs_schedule's variant:
+# 6 = 256 x 4 with Schur-complement slots, 9 = 256 x 4 without, 1 = 256 x 2),
+# from ncu captures of the tree kernels with that schedule pinned (mean of the
+# warm-up and timed launches); a shape not listed has no figure (None).
+TRAFFIC_BYTES = {("fp32r", 6): 5.7475e9 + 4.3202e9, ("fp32r", 9): 2.2075e9 + 3.8513e9,
+                 ("fp64", 1): 3.4121e9 + 4.2817e9}
 NOMINAL_FP64_FMA_PER_CLK_PER_SM = 2
 NOMINAL_FP32_FMA_PER_CLK_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
@@ -146,37 +148,52 @@ def pipe_fracs(ops, n_entries, ms, peaks, sms, sm_mhz):
     t = ms * 1e-3
     f64 = (2 * ops["dfma"] + ops["dadd"] + ops["dmul"]) * n_entries / t
     i64 = (ops["dfma"] + ops["dadd"] + ops["dmul"]) * n_entries / t
-    f32i = ops["fp32"] * n_entries / t
+    f32i = (ops["fp32"] or 0.0) * n_entries / t
     nominal64 = 2 * NOMINAL_FP64_FMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6
     nominal32 = 2 * NOMINAL_FP32_FMA_PER_CLK_PER_SM * sms * sm_mhz * 1e6
-    return {
+    out = {
         "fp64": {"achieved_tflops": f64 / 1e12, "peak_tflops": peaks["fp64_flops"] / 1e12,
                  "frac": f64 / peaks["fp64_flops"], "frac_of_nominal": f64 / nominal64,
                  "pipe_instr_per_entry": ops["dfma"] + ops["dadd"] + ops["dmul"],
                  "pipe_frac": i64 / (peaks["fp64_flops"] / 2)},
-        "fp32": {"instr_per_entry": ops["fp32"], "pipe_frac": f32i / (peaks["fp32_flops"] / 2),
-                 "pipe_frac_of_nominal": f32i / (nominal32 / 2)},
     }
+    if ops["fp32"] is not None:
+        out["fp32"] = {"instr_per_entry": ops["fp32"], "pipe_frac": f32i / (peaks["fp32_flops"] / 2),
+                       "pipe_frac_of_nominal": f32i / (nominal32 / 2)}
+    return out
+
+
+def order5_traffic(prec, M):
+    """ncu DRAM bytes of the order-5 kernel under the schedule this process runs, or None."""
+    import paper_2511_14923_gb300 as gbs
+    if M != 144:
+        return None
+    return TRAFFIC_BYTES.get((prec, gbs.schedule(M, 5, prec)["variant"]))
 
 
 def tree_roofline(prec, M, d, kmax, ms, peaks, sms, sm_mhz, hbm):
+    import paper_2511_14923_gb300 as gbs
     n = comb(M, d)
     alg = tree_bytes(M, d, kmax)
     out = {"kernel": f"tree_kernel<{d}, kappa, {prec}>", "entries": n, "ms": ms,
            "dram": {"algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm[0],
                     "frac": alg / (ms * 1e-3) / 1e9 / hbm[0]}}
     ops = OPS_PER_ENTRY.get((prec, d))
+    if ops and prec == "fp32r" and gbs.schedule(M, kmax, prec)["variant"] == 9:
+        ops = {**ops, "fp32": None}  # same FP64 work; the slot-free form's FP32 count was not captured
     if ops:
         out.update(pipe_fracs(ops, n, ms, peaks, sms, sm_mhz))
-    if d == 5 and M == 144 and TRAFFIC_BYTES.get(prec):
-        out["dram"]["traffic"] = TRAFFIC_BYTES[prec]
-        out["dram"]["traffic_over_algorithmic"] = TRAFFIC_BYTES[prec] / alg
+    traffic = order5_traffic(prec, M) if d == 5 else None
+    if traffic:
+        out["dram"]["traffic"] = traffic
+        out["dram"]["traffic_over_algorithmic"] = traffic / alg
     return out
 
 
 def headline_roofline(prec, M, kmax, order_ms, peaks, sms, sm_mhz, hbm):
     """The dominant kernel (order kmax) in the contract's form, its pipes, and every
     prefix-tree kernel of the call."""
+    import paper_2511_14923_gb300 as gbs
     kernels = [tree_roofline(prec, M, d, kmax, order_ms[d], peaks, sms, sm_mhz, hbm)
                for d in range(4, kmax + 1) if order_ms[d] > 0]
     top = kernels[-1]
@@ -185,7 +202,8 @@ def headline_roofline(prec, M, kmax, order_ms, peaks, sms, sm_mhz, hbm):
             "achieved": fp64["achieved_tflops"] if fp64 else None,
             "peak": peaks["fp64_flops"] / 1e12, "unit": "TFLOP/s",
             "frac": fp64["frac"] if fp64 else None,
-            "traffic": TRAFFIC_BYTES.get(prec) if M == 144 else None,
+            "traffic": order5_traffic(prec, M) if kmax == 5 else None,
+            "schedule": gbs.schedule(M, kmax, prec),
             "peak_source": "measured in this run by gbs_pipe_peaks (sustained FP64 FMA throughput), of measured",
             "kernel_ms": order_ms[kmax], "order_ms": list(order_ms),
             "pipes": {k: top[k] for k in ("fp64", "fp32", "dram") if k in top},

@@ -289,8 +289,10 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
    per shared-memory batch (16, 64), CTA shape (512 threads x 1 per SM, 256 x 2
    per SM when M <= 577; for GBS_FP32_REFINED also 640 x 1, 256 x 3 when
    M <= 577, 768 x 1 with a larger shared-memory batch area, 384 x 2 when
-   M <= 961, 256 x 4 when M <= 385, and the 256 x 4 and 256 x 3 shapes in
-   thread-block clusters whose CTAs share one Schur-complement slot) -- and records
+   M <= 961, 256 x 4 when M <= 385, the 256 x 4 and 256 x 3 shapes in
+   thread-block clusters whose CTAs share one Schur-complement slot, and 256 x 4
+   without slots when M <= 161, forming each Schur-complement block from the
+   item's elimination rows where it is used) -- and records
    the fastest in a process-wide table that
    later forward calls of that shape use. If the environment variable
    GBS_AUTOTUNE_CACHE names a file, the table is read from it on first use and
@@ -301,6 +303,17 @@ int gbs_sample(const double *kappa, int M, int K, const int *orders, int n_sampl
    identical tables. */
 int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precision, void *workspace,
                  size_t ws_bytes, void *cuda_stream, float *best_ms_out);
+
+/* Schedule the forward calls of (M, kmax, precision) run on the current device:
+   the one gbs_autotune recorded (or read from GBS_AUTOTUNE_CACHE), else the
+   default. schedule_out[3] (host) = {CTA shape (0: 512 threads x 1 per SM,
+   1: 256 x 2, refined only 2: 640 x 1, 3: 256 x 3, 4: 768 x 1, 5: 384 x 2,
+   6: 256 x 4, 7 and 8: 6 and 3 in thread-block clusters, 9: 6 without
+   Schur-complement slots), items per CTA slot, children per shared-memory
+   batch}, after the fallback to 512 x 1 for a shape that does not admit M.
+   Host only; allocates nothing. Returns GBS_OK, GBS_ERR_INVALID_ARG (bad
+   shape or precision, NULL schedule_out) or GBS_ERR_CUDA (no device). */
+int gbs_schedule(int M, int kmax, int precision, int *schedule_out);
 
 /* ---------------------------------------------------------------- ragged batches */
 

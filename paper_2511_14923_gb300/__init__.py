@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
     L.gbs_status_code.argtypes = [ctypes.c_uint]; L.gbs_status_code.restype = i32
     L.gbs_autotune.argtypes = [vp, i32, i32, vp, i32, vp, sz, vp, ctypes.POINTER(ctypes.c_float)]
     L.gbs_autotune.restype = i32
+    L.gbs_schedule.argtypes = [i32, i32, i32, ctypes.POINTER(i32)]; L.gbs_schedule.restype = i32
     L.gbs_timing.argtypes = [i32]; L.gbs_timing.restype = i32
     L.gbs_timing_read.argtypes = [ctypes.POINTER(ctypes.c_float)]; L.gbs_timing_read.restype = i32
     L.gbs_timing_read_backward.argtypes = [ctypes.POINTER(ctypes.c_float)]
@@ -603,6 +604,13 @@ def autotune(V, kmax, precision="fp32r", workspace=None) -> float:
     _check(lib().gbs_autotune(_vp(V), M, kmax, _vp(out), PRECISIONS[precision], ctypes.c_void_p(ws.ptr), ws.nbytes,
                               ctypes.c_void_p(st.cuda_stream), ctypes.byref(ms)))
     return float(ms.value)
+
+
+def schedule(M: int, kmax: int, precision: str = "fp32r") -> dict:
+    """Schedule the forward calls of this shape run on the current device (gbs_schedule)."""
+    arr = (ctypes.c_int * 3)()
+    _check(lib().gbs_schedule(M, kmax, PRECISIONS[precision], arr))
+    return {"variant": arr[0], "grain": arr[1], "ccap": arr[2]}
 
 
 def timing(on: bool) -> None:

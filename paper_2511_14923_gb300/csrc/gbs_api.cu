@@ -486,6 +486,21 @@ int gbs_autotune(const double *V, int M, int kmax, double *kappa_out, int precis
     return ok();
 }
 
+int gbs_schedule(int M, int kmax, int precision, int *schedule_out) {
+    if (!schedule_out) return fail(GBS_ERR_INVALID_ARG, "schedule_out is NULL");
+    if (!valid_mk(M, kmax)) return fail(GBS_ERR_INVALID_ARG, "%s", gbs::shape_message(M, kmax).c_str());
+    if (precision != GBS_FP64 && precision != GBS_FP32_REFINED)
+        return fail(GBS_ERR_INVALID_ARG, "precision must be GBS_FP64 or GBS_FP32_REFINED");
+    const int sms = device_sms();
+    if (sms <= 0) return fail(GBS_ERR_CUDA, "no current CUDA device");
+    const gbs::TreeCfg cfg = gbs::tuned_cfg(sms, M, kmax, precision);
+    schedule_out[0] = gbs::effective_variant(cfg.variant, M, precision);
+    schedule_out[1] = cfg.grain > 0 ? cfg.grain : gbs::kDefaultCfg.grain;
+    schedule_out[2] = cfg.ccap > 0 && cfg.ccap <= gbs::kMaxChildren ? cfg.ccap : gbs::kDefaultCfg.ccap;
+    if (schedule_out[0] == 9 && schedule_out[2] > gbs::kNoSlotCC) schedule_out[2] = gbs::kNoSlotCC;
+    return ok();
+}
+
 int gbs_vacuum_probs(const double *V, int M, int kmax, double *p0_out, int precision, void *workspace,
                      size_t ws_bytes, void *cuda_stream) {
     return run_forward(gbs::MODE_P0, V, M, kmax, p0_out, precision, workspace, ws_bytes, cuda_stream);

@@ -58,6 +58,8 @@ struct TreeCfg {
     int grain, ccap, variant;
 };
 constexpr TreeCfg kDefaultCfg{2, 64, 0};
+// Most children per shared-memory batch any CTA shape has room for.
+constexpr int kMaxChildren = 64;
 // Largest M the 256-thread variant accepts (its shared x-entry area holds 576 modes).
 constexpr int kVariant1MaxM = 577;
 // x-entries per batch of the 768-thread refined variant (one CTA per SM).
@@ -77,6 +79,17 @@ constexpr int kVariant9MaxM = kNoSlotYC + 1;  // order 4 reaches c4 = M - 1
 // 256 x 3 shapes in thread-block clusters of 4 and 3 CTAs sharing one slot, 9 the
 // 256 x 4 shape without slots.
 constexpr int kNumVariants = 10;
+// CTA shape a forward call of (M, precision) runs for a recorded variant: the
+// shapes that do not admit M (or the precision) fall back to 512 x 1.
+inline int effective_variant(int variant, int M, int precision) {
+    if (variant == 1 || variant == 3 || variant == 8) return M <= kVariant1MaxM && (variant == 1 || precision == 1) ? variant : 0;
+    if (precision != 1) return 0;
+    if (variant == 2 || variant == 4) return variant;
+    if (variant == 5) return M <= kVariant5MaxM ? 5 : 0;
+    if (variant == 6 || variant == 7) return M <= kVariant6MaxM ? variant : 0;
+    if (variant == 9) return M <= kVariant9MaxM ? 9 : 0;
+    return 0;
+}
 // Whether a variant runs in clusters (the batched kernel has no clustered form).
 inline bool variant_clustered(int v) { return v == 7 || v == 8; }
 

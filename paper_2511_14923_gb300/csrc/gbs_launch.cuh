@@ -226,29 +226,23 @@ static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t 
         // displaced states: FP64, one 512-thread CTA per multiprocessor
         return launch_tree_v<D, MODE, 0, TREE_THREADS, XCAP, 1, true>(a, write_p0, st);
     } else {
-        if (a.variant == 1 && a.M <= kVariant1MaxM)
-            return launch_tree_v<D, MODE, PREC, 256, 576, 2, false>(a, write_p0, st);
+        const int v = effective_variant(a.variant, a.M, PREC);
+        if (v == 1) return launch_tree_v<D, MODE, PREC, 256, 576, 2, false>(a, write_p0, st);
         if constexpr (PREC == 1) {
             // register-lean refined kernels: 20 warps in one CTA, 3 CTAs of 8 warps,
             // 24 warps in one CTA with room for about 3.5x more children per batch,
             // 2 CTAs of 12 warps with room for about 1.7x more, or 4 CTAs of 8 warps
             // (64 registers) with room for a third fewer
-            if (a.variant == 2) return launch_tree_v<D, MODE, PREC, 640, XCAP, 1, false>(a, write_p0, st);
-            if (a.variant == 3 && a.M <= kVariant1MaxM)
-                return launch_tree_v<D, MODE, PREC, 256, 576, 3, false>(a, write_p0, st);
-            if (a.variant == 4) return launch_tree_v<D, MODE, PREC, 768, kWideXC, 1, false>(a, write_p0, st);
-            if (a.variant == 5 && a.M <= kVariant5MaxM)
-                return launch_tree_v<D, MODE, PREC, 384, kPairXC, 2, false>(a, write_p0, st);
-            if (a.variant == 6 && a.M <= kVariant6MaxM)
-                return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false>(a, write_p0, st);
+            if (v == 2) return launch_tree_v<D, MODE, PREC, 640, XCAP, 1, false>(a, write_p0, st);
+            if (v == 3) return launch_tree_v<D, MODE, PREC, 256, 576, 3, false>(a, write_p0, st);
+            if (v == 4) return launch_tree_v<D, MODE, PREC, 768, kWideXC, 1, false>(a, write_p0, st);
+            if (v == 5) return launch_tree_v<D, MODE, PREC, 384, kPairXC, 2, false>(a, write_p0, st);
+            if (v == 6) return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false>(a, write_p0, st);
             // the 256 x 4 and 256 x 3 shapes in clusters that share one slot per U
-            if (a.variant == 7 && a.M <= kVariant6MaxM)
-                return launch_tree_cl<D, MODE, PREC, 256, kQuadXC, 4, 4>(a, write_p0, st);
-            if (a.variant == 8 && a.M <= kVariant1MaxM)
-                return launch_tree_cl<D, MODE, PREC, 256, 576, 3, 3>(a, write_p0, st);
+            if (v == 7) return launch_tree_cl<D, MODE, PREC, 256, kQuadXC, 4, 4>(a, write_p0, st);
+            if (v == 8) return launch_tree_cl<D, MODE, PREC, 256, 576, 3, 3>(a, write_p0, st);
             // 256 x 4 without slots: Schur-complement blocks formed from Y where used
-            if (a.variant == 9 && a.M <= kVariant9MaxM)
-                return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false, kNoSlotCC, kNoSlotYC>(a, write_p0, st);
+            if (v == 9) return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false, kNoSlotCC, kNoSlotYC>(a, write_p0, st);
         }
         return launch_tree_v<D, MODE, PREC, TREE_THREADS, XCAP, 1, false>(a, write_p0, st);
     }

@@ -15,7 +15,7 @@ namespace gbs {
 constexpr int FLAT_THREADS = 256;
 constexpr int TREE_THREADS = 512;
 constexpr int XCAP = 1152;  // per-batch x-entries in shared memory (>= GBS_MAX_MODES)
-constexpr int CCAP = 64;    // per-batch children
+constexpr int CCAP = kMaxChildren;  // per-batch children
 
 // ---------------------------------------------------------------- shared combine step
 

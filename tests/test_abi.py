@@ -94,6 +94,11 @@ def test_compute_entry_rejects_bad_arguments_without_launching():
     assert L.gbs_cumulants(vp(0), 8, 9, vp(0), 0, vp(0), 0, vp(0)) == 1
     assert L.gbs_vacuum_probs(vp(0), 8, 3, vp(0), 5, vp(0), 0, vp(0)) == 1
     assert b"kmax" in L.gbs_last_error() or b"precision" in L.gbs_last_error()
+    # the schedule query checks its arguments before it looks for a device
+    arr = (ctypes.c_int * 3)()
+    assert L.gbs_schedule(144, 5, 1, None) == 1
+    assert L.gbs_schedule(144, 6, 1, arr) == 1
+    assert L.gbs_schedule(144, 5, 7, arr) == 1
 
 
 def test_large_mode_counts_for_low_orders():

@@ -69,12 +69,13 @@ def test_pipe_peaks_probe():
 
 
 PINNED = r"""
-import sys, hashlib, torch
+import sys, hashlib, json, torch
 sys.path.insert(0, {root!r})
 import synthetic, paper_2511_14923_gb300 as gbs
 inst = synthetic.random_instance(40, 5, seed=12, r_range=(0.5, 1.4), eta_range=(0.3, 0.5))
 t = gbs.cumulants(torch.from_numpy(inst.V).cuda(), 5, {prec!r})
 print(hashlib.sha256(t.cpu().numpy().tobytes()).hexdigest())
+print(json.dumps(gbs.schedule(40, 5, {prec!r})))
 """
 
 
@@ -93,5 +94,8 @@ def test_every_cta_shape_gives_identical_table(tmp_path, prec, variants):
             out = subprocess.run([sys.executable, "-c", PINNED.format(root=ROOT, prec=prec)], env=env,
                                  capture_output=True, text=True)
             assert out.returncode == 0, out.stderr
-            digests.add(out.stdout.strip())
+            digest, sched = out.stdout.strip().splitlines()
+            digests.add(digest)
+            # gbs_schedule reports the pinned schedule (the slot-free shape has room for 24 children)
+            assert json.loads(sched) == {"variant": v, "grain": grain, "ccap": min(ccap, 24) if v == 9 else ccap}
     assert len(digests) == 1
