@@ -368,17 +368,22 @@ __global__ void __launch_bounds__(256) zgemm_kernel(Args<R> a, int t, uint64_t r
 // in tensor memory (the dropped Alo Blo term is ~2^-22 relative). A CTA of 128
 // threads owns 128 rows x 256 samples. W arrives from wtc_kernel already split
 // and laid out as the MMA's K-major core matrices (8 rows x 16 bytes, no
-// swizzle), one contiguous 64 KB block per 32-wide K chunk and sample tile, and
-// is brought in by one TMA bulk copy per chunk; thread i splits and stages row i
-// of the cumulant segments. One elected thread issues the MMAs. Two stages, each
-// with a "full" mbarrier (the bulk copy's bytes) and an "empty" one (the MMAs'
-// commit), overlap the staging of chunk c+1 with the MMAs of chunk c. Every wait
-// is bounded; one that runs out sets ST_TIMEOUT in the status word.
-constexpr int TC_M = 128, TC_N = 256, TC_KC = 32;
-constexpr int TC_AB = TC_M * TC_KC * 4;         // bytes of one A copy per stage (16 KB)
-constexpr int TC_BB = TC_N * TC_KC * 4;         // bytes of one B copy per stage (32 KB)
+// swizzle), one contiguous block per TC_KC-wide K chunk and sample tile, and
+// is brought in by one TMA bulk copy per chunk; the rows (cumulant segments)
+// arrive the same way from atc_kernel. One elected thread issues the MMAs. A
+// ring of TC_NS stages, each with a "full" mbarrier (the bulk copies' bytes) and
+// an "empty" one (the MMAs' commit), keeps TC_NS - 1 chunks loading while the
+// MMAs of one run; the ring takes 96 KB of shared memory, so two CTAs share a
+// multiprocessor (and its 512 tensor-memory columns) and one's epilogue
+// overlaps the other's MMAs. Every wait is bounded; one that runs out sets ST_TIMEOUT in the status
+// word.
+constexpr int TC_M = 128, TC_N = 256, TC_KC = 8, TC_NS = 4;  // TC_NS stages of TC_KC-wide chunks
+constexpr int TC_ACH = TC_M * TC_KC;            // floats of one A copy (hi or lo) of one chunk
+constexpr int TC_BCH = TC_N * TC_KC;            // floats of one B copy of one chunk
+constexpr int TC_AB = TC_M * TC_KC * 4;         // bytes of one A copy per stage (4 KB)
+constexpr int TC_BB = TC_N * TC_KC * 4;         // bytes of one B copy per stage (8 KB)
 constexpr int TC_STAGE = 2 * TC_AB + 2 * TC_BB;  // A hi, A lo, B hi, B lo
-constexpr int TC_SMEM = 2 * TC_STAGE + 256;
+constexpr int TC_SMEM = TC_NS * TC_STAGE + 256;  // stages, then 2 x TC_NS mbarriers, TMEM slot, flag
 // instruction descriptor: D f32, A and B tf32, both K-major, N = 256, M = 128
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
@@ -392,9 +397,9 @@ __device__ __forceinline__ uint32_t tc_off(int r, int k) {
 }
 
 // shared-memory matrix descriptor: K-major, no swizzle; leading byte offset 128
-// (next core matrix along K), stride byte offset 1024 (next group of 8 rows)
+// (next core matrix along K), stride byte offset 32 TC_KC (next group of 8 rows)
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)((32 * TC_KC) >> 4) << 32) |
            ((uint64_t)1 << 46);
 }
 
@@ -464,9 +469,9 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 // W_t split into TF32 hi / lo in the tensor-core tile layout: element (r, s),
-// r < 32 ceil(D / 32) (zero beyond D), at float offset
-// ((c nsb + sb) 2 + part) 8192 + tc_off(s % 256, r % 32) / 4, c = r / 32,
-// sb = s / 256, nsb = S / 256. A thread forms four consecutive r (one 16-byte
+// r < KC ceil(D / KC) (zero beyond D; KC = TC_KC inner entries per chunk), at
+// float offset ((c nsb + sb) 2 + part) 256 KC + tc_off(s % 256, r % KC) / 4,
+// c = r / KC, sb = s / 256, nsb = S / 256. A thread forms four consecutive r (one 16-byte
 // row of a core matrix) of one sample, so 8 consecutive samples write one
 // 128-byte line. Grid: (samples / ETB, quads of r).
 template <int K>
@@ -506,16 +511,16 @@ __global__ void __launch_bounds__(ETB) wtc_kernel(Args<float> a, int t, int D) {
         h.y = to_tf32(v[1]); l.y = to_tf32(v[1] - h.y);
         h.z = to_tf32(v[2]); l.z = to_tf32(v[2] - h.z);
         h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
-        const size_t blk = ((size_t)(r0 / TC_KC) * nsb + sb) * 2 * 8192;
+        const size_t blk = ((size_t)(r0 / TC_KC) * nsb + sb) * 2 * TC_BCH;
         const uint32_t o = tc_off(sl, r0 % TC_KC) / 4;
         *reinterpret_cast<float4 *>(a.W + blk + o) = h;
-        *reinterpret_cast<float4 *>(a.W + blk + 8192 + o) = l;
+        *reinterpret_cast<float4 *>(a.W + blk + TC_BCH + o) = l;
     }
 }
 
 // The rows of the step product (cumulant segments) split into TF32 hi / lo and
-// laid out like W: row tile rt (128 rows), chunk c (32 inner entries) at float
-// offset (rt nk + c) 2 4096, hi then lo, each in the core-matrix layout.
+// laid out like W: row tile rt (128 rows), chunk c (TC_KC inner entries) at
+// float offset (rt nk + c) 2 128 TC_KC, hi then lo, each in the core-matrix layout.
 // Rows beyond `rows` and entries beyond D are zero. Grid: (row tiles, chunks),
 // 128 threads, thread i = row i of the tile.
 template <int K>
@@ -525,7 +530,7 @@ __global__ void __launch_bounds__(128) atc_kernel(Args<float> a, int t, uint64_t
     uint64_t kb = 0, dst = 0;
     int kind = -1;
     if (q < rows) zrow(K, a.M, t, q, a.off, kb, kind, dst);
-    float *blk = a.At + ((size_t)rt * nk + c) * 2 * 4096;
+    float *blk = a.At + ((size_t)rt * nk + c) * 2 * TC_ACH;
     const float *kp = a.kap + kb;
 #pragma unroll 2
     for (int j = 0; j < TC_KC; j += 4) {
@@ -540,28 +545,30 @@ __global__ void __launch_bounds__(128) atc_kernel(Args<float> a, int t, uint64_t
         h.w = to_tf32(v[3]); l.w = to_tf32(v[3] - h.w);
         const uint32_t o = tc_off(tid, j) / 4;
         *reinterpret_cast<float4 *>(blk + o) = h;
-        *reinterpret_cast<float4 *>(blk + 4096 + o) = l;
+        *reinterpret_cast<float4 *>(blk + TC_ACH + o) = l;
     }
 }
 
 // Z rows of one 128-row tile x 256 samples. Thread 0 streams both operands by
-// TMA bulk copies (32 KB of A, 64 KB of W per 32-wide chunk) into two stages and
-// issues the MMAs; chunk c+1 is loaded into the stage of chunk c-1 once the MMAs
-// of chunk c-1 have completed, while those of chunk c run. All threads then read
+// TMA bulk copies (A: 128 rows, W: 256 samples, hi and lo, per TC_KC-wide
+// chunk) into a ring of TC_NS stages and issues the MMAs; chunk c-1+TC_NS is
+// loaded into the stage of chunk c-1 once the MMAs of chunk c-1 have completed,
+// while those of chunk c run. All threads then read
 // the accumulator (thread i = row i) and write the rows out.
 template <int K>
-__global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint64_t rows, int D) {
+__global__ void __launch_bounds__(128, 2) ztc_kernel(Args<float> a, int t, uint64_t rows, int D) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);
-    uint64_t *empty = full + 2;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * TC_STAGE + 64);
-    int *flag = reinterpret_cast<int *>(smem + 2 * TC_STAGE + 128);
+    static_assert(TC_NS <= 8, "barrier area");
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TC_NS * TC_STAGE);
+    uint64_t *empty = full + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + TC_NS * TC_STAGE + 128);
+    int *flag = reinterpret_cast<int *>(smem + TC_NS * TC_STAGE + 192);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint64_t m0 = (uint64_t)blockIdx.x * TC_M;
     const int rt = blockIdx.x, sb = blockIdx.y, s0 = sb * TC_N, nsb = a.S / TC_N;
     const int nk = (D + TC_KC - 1) / TC_KC;
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < TC_NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
@@ -580,32 +587,30 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
     const uint32_t tmem = *tslot;
     if (tid == 0) {
         const uint32_t sbase = smem_u32(smem);
-        const float *Ab = a.At + (size_t)rt * nk * 2 * 4096;
-        const float *Wb = a.W + (size_t)sb * 2 * 8192;
+        const float *Ab = a.At + (size_t)rt * nk * 2 * TC_ACH;
+        const float *Wb = a.W + (size_t)sb * 2 * TC_BCH;
         auto load = [&](int c) {
-            unsigned char *sp = smem + (c & 1) * TC_STAGE;
-            mbar_expect(&full[c & 1], 2 * TC_AB + 2 * TC_BB);
-            tma_bulk(sp, Ab + (size_t)c * 2 * 4096, 2 * TC_AB, &full[c & 1]);
-            tma_bulk(sp + 2 * TC_AB, Wb + (size_t)c * nsb * 2 * 8192, 2 * TC_BB, &full[c & 1]);
+            const int st = c % TC_NS;
+            unsigned char *sp = smem + st * TC_STAGE;
+            mbar_expect(&full[st], 2 * TC_AB + 2 * TC_BB);
+            tma_bulk(sp, Ab + (size_t)c * 2 * TC_ACH, 2 * TC_AB, &full[st]);
+            tma_bulk(sp + 2 * TC_AB, Wb + (size_t)c * nsb * 2 * TC_BCH, 2 * TC_BB, &full[st]);
         };
-        // chunk c uses stage c & 1 and completes phase (c >> 1) & 1 of its barriers;
-        // nl chunks loaded, nf of them waited for (full), nc committed, ne of those
-        // waited for (empty)
+        // chunk c uses stage c % TC_NS and completes phase (c / TC_NS) & 1 of its
+        // barriers; nl chunks loaded, nf of them waited for (full), nc committed,
+        // ne of those waited for (empty)
         int nl = 0, nf = 0, nc = 0, ne = 0;
         const int lim = a.wait_limit;
-        auto wait_full = [&](int c) { return mbar_wait(&full[c & 1], (uint32_t)(c >> 1) & 1u, lim); };
-        auto wait_empty = [&](int c) { return mbar_wait(&empty[c & 1], (uint32_t)(c >> 1) & 1u, lim); };
+        auto wait_full = [&](int c) { return mbar_wait(&full[c % TC_NS], (uint32_t)(c / TC_NS) & 1u, lim); };
+        auto wait_empty = [&](int c) { return mbar_wait(&empty[c % TC_NS], (uint32_t)(c / TC_NS) & 1u, lim); };
         bool ok = true;
-        if (!a.no_loads) {
-            load(0);
-            ++nl;
-            if (nk > 1) {
-                load(1);
+        if (!a.no_loads)
+            for (int c = 0; c < TC_NS && c < nk; ++c) {
+                load(c);
                 ++nl;
             }
-        }
         for (int c = 0; c < nk && ok; ++c) {
-            const int st = c & 1;
+            const int st = c % TC_NS;
             ok = wait_full(c);
             if (!ok) break;
             ++nf;
@@ -622,17 +627,18 @@ __global__ void __launch_bounds__(128, 1) ztc_kernel(Args<float> a, int t, uint6
             }
             tc_commit(&empty[st]);
             ++nc;
-            // refill the other stage with chunk c+1 once the MMAs of chunk c-1 are done
-            if (c >= 1 && c + 1 < nk) {
+            // refill the stage of chunk c-1 with chunk c-1+TC_NS once its MMAs are
+            // done (those of chunk c are queued behind them meanwhile)
+            if (c >= 1 && c - 1 + TC_NS < nk) {
                 ok = wait_empty(c - 1);
                 if (ok) {
                     ++ne;
-                    load(c + 1);
+                    load(c - 1 + TC_NS);
                     ++nl;
                 }
             }
         }
-        // the loop waited for chunks 0 .. nk-3; wait for the last two
+        // the loop waited for chunks 0 .. nk-1-TC_NS; wait for the rest
         while (ok && ne < nc) {
             ok = wait_empty(ne);
             if (ok) ++ne;
@@ -1320,7 +1326,7 @@ SamplerLayout sampler_layout(int M, int K, int S, int precision) {
             const uint64_t rows = K == 3   ? 1 + (uint64_t)(M - t)
                                   : K == 4 ? 1 + 2 * (uint64_t)(M - t)
                                            : 1 + 2 * (uint64_t)(M - t) + cb(M - t, 2);
-            const size_t n = (size_t)((rows + 127) / 128) * ((D + 31) / 32) * 8192;
+            const size_t n = (size_t)((rows + TC_M - 1) / TC_M) * ((D + TC_KC - 1) / TC_KC) * 2 * TC_ACH;
             if (n > at) at = n;
         }
     L.At = off;
