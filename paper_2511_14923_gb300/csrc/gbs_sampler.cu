@@ -660,22 +660,41 @@ __global__ void __launch_bounds__(128, 2) ztc_kernel(Args<float> a, int t, uint6
         uint64_t kb = 0, dst = 0;
         int kind = -1;
         if (m0 + tid < rows) zrow(K, a.M, t, m0 + tid, a.off, kb, kind, dst);
-        float *out = kind == 0 ? a.G
+        float *out = kind < 0    ? nullptr
+                   : kind == 0 ? a.G
                    : kind == 1 ? a.Z + dst * a.S
                    : kind == 2 ? a.Z5 + dst * a.S
                                : a.X + dst * a.S;
+        // The warp's 32 rows leave through shared memory (the ring is idle now):
+        // a lane holds 32 columns of its own row after tcgen05.ld; the warp
+        // writes them to a 32 x 36-float tile and reads them back as 8 lanes per
+        // row, so every store instruction writes four whole 128-byte row pieces.
+        const int lane = tid & 31, rsub = lane >> 3, c4 = (lane & 7) * 4;
+        float *tile = reinterpret_cast<float *>(smem) + warp * 32 * 36;
+        float *optr[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int src = 4 * i + rsub;  // row of the tile this lane stores in round i
+            const unsigned long long p = __shfl_sync(0xffffffffu, (unsigned long long)out, src);
+            optr[i] = reinterpret_cast<float *>(p);
+        }
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int cc = 0; cc < TC_N / 32; ++cc) {
             uint32_t v[32];
             tc_ld32(lane_base + (uint32_t)(cc * 32), v);
-            if (kind >= 0) {
-                float4 *o4 = reinterpret_cast<float4 *>(out + s0 + cc * 32);
+            float4 *row = reinterpret_cast<float4 *>(tile + lane * 36);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    o4[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                        __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            for (int q = 0; q < 8; ++q)
+                row[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                     __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 w = *reinterpret_cast<const float4 *>(tile + (4 * i + rsub) * 36 + c4);
+                if (optr[i]) *reinterpret_cast<float4 *>(optr[i] + s0 + cc * 32 + c4) = w;
             }
+            __syncwarp();
         }
     }
     tc_fence_before();
