@@ -480,6 +480,11 @@ __global__ void __launch_bounds__(ETB) wtc_kernel(Args<float> a, int t, int D) {
     const int Dp = (D + TC_KC - 1) / TC_KC * TC_KC;
     const int nsb = a.S / TC_N, sb = s / TC_N, sl = s % TC_N;
     Spins<float> sp(a, s), sd(a, s);
+    // K = 4, 5: pair r = (e, d) with e < t - 1 is entry C(t-2, 3) + r of the p2
+    // table (row t - 1 lists its pairs in colex order); e = t - 1 reads P1~[t-2][d]
+    const size_t S = (size_t)a.S;
+    const uint64_t rowlen = K == 3 ? 0 : cb(t - 2, 2);
+    const float *q2 = a.P2 + (K != 3 && t >= 4 ? cb(t - 2, 3) : 0) * S + s;
     for (int qd = blockIdx.y; qd < Dp / 4; qd += gridDim.y) {
         const int r0 = 4 * qd;
         float v[4];
@@ -498,7 +503,10 @@ __global__ void __launch_bounds__(ETB) wtc_kernel(Args<float> a, int t, int D) {
                 if (K == 3) {
                     v[j] = p1(a, t - 1, r + 1, s) * sp(r + 1);
                 } else {
-                    v[j] = p2(a, t - 1, e, d, s) * sp(e) * sd(d);
+                    const float p = (uint64_t)r < rowlen ? q2[(size_t)r * S]
+                                    : d == t - 2         ? a.P[(size_t)(t - 3) * S + s]
+                                                         : a.P1[i_p1(t - 2, d) * S + s];
+                    v[j] = p * sp(e) * sd(d);
                     if (++d == e) {  // next pair in colex order
                         ++e;
                         d = 1;
