@@ -179,8 +179,11 @@ def tree_roofline(prec, M, d, kmax, ms, peaks, sms, sm_mhz, hbm):
            "dram": {"algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": hbm[0],
                     "frac": alg / (ms * 1e-3) / 1e9 / hbm[0]}}
     ops = OPS_PER_ENTRY.get((prec, d))
-    if ops and prec == "fp32r" and gbs.schedule(M, kmax, prec)["variant"] == 9:
-        ops = {**ops, "fp32": None}  # same FP64 work; the slot-free form's FP32 count was not captured
+    v = gbs.schedule(M, kmax, prec)["variant"]
+    if ops and prec == "fp32r" and (v == 9 or (v == 6 and d == 4 and M <= 161)):
+        # the slot-free form (order 4 of the 256 x 4 shape runs it too): same FP64
+        # work, its FP32 count was not captured
+        ops = {**ops, "fp32": None}
     if ops:
         out.update(pipe_fracs(ops, n, ms, peaks, sms, sm_mhz))
     traffic = order5_traffic(prec, M) if d == 5 else None

@@ -237,7 +237,14 @@ static cudaError_t launch_tree(const FwdArgs &a_in, bool write_p0, cudaStream_t 
             if (v == 3) return launch_tree_v<D, MODE, PREC, 256, 576, 3, false>(a, write_p0, st);
             if (v == 4) return launch_tree_v<D, MODE, PREC, 768, kWideXC, 1, false>(a, write_p0, st);
             if (v == 5) return launch_tree_v<D, MODE, PREC, 384, kPairXC, 2, false>(a, write_p0, st);
-            if (v == 6) return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false>(a, write_p0, st);
+            if (v == 6) {
+                // order 4 of the 256 x 4 shape runs without slots where it can: its items
+                // are small (one U = {c4} split into many stride classes), so rebuilding
+                // the slot per item cost more than forming the blocks in place (same bits)
+                if (D == 4 && a.M <= kVariant9MaxM)
+                    return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false, kNoSlotCC, kNoSlotYC>(a, write_p0, st);
+                return launch_tree_v<D, MODE, PREC, 256, kQuadXC, 4, false>(a, write_p0, st);
+            }
             // the 256 x 4 and 256 x 3 shapes in clusters that share one slot per U
             if (v == 7) return launch_tree_cl<D, MODE, PREC, 256, kQuadXC, 4, 4>(a, write_p0, st);
             if (v == 8) return launch_tree_cl<D, MODE, PREC, 256, 576, 3, 3>(a, write_p0, st);
