@@ -60,6 +60,14 @@ OPS_PER_ENTRY = {
     ("fp64", 5): {"dfma": 36.149, "dadd": 0.001, "dmul": 8.406, "fp32": 4.592},
     ("fp64", 4): {"dfma": 33.458, "dadd": 0.013, "dmul": 8.375, "fp32": 13.474},
 }
+# The same counts for the slot-free refined form (order 4 of the 256 x 4 shape at
+# grain 2, and order 5 of the slot-free shape): ncu's DFMA and FP32 counters of
+# those kernels; their FP64 arithmetic is the slot kernels', so DADD and DMUL are
+# taken from the rows above.
+OPS_PER_ENTRY_NOSLOT = {
+    ("fp32r", 5): {"dfma": 15.021, "dadd": 0.014, "dmul": 0.019, "fp32": 477.89},
+    ("fp32r", 4): {"dfma": 8.022, "dadd": 0.021, "dmul": 1.022, "fp32": 452.21},
+}
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # order-5 kernel at M=144, by precision and CTA shape (gbs_schedule's variant:
 # 6 = 256 x 4 with Schur-complement slots, 9 = 256 x 4 without, 1 = 256 x 2),
@@ -180,10 +188,8 @@ def tree_roofline(prec, M, d, kmax, ms, peaks, sms, sm_mhz, hbm):
                     "frac": alg / (ms * 1e-3) / 1e9 / hbm[0]}}
     ops = OPS_PER_ENTRY.get((prec, d))
     v = gbs.schedule(M, kmax, prec)["variant"]
-    if ops and prec == "fp32r" and (v == 9 or (v == 6 and d == 4 and M <= 161)):
-        # the slot-free form (order 4 of the 256 x 4 shape runs it too): same FP64
-        # work, its FP32 count was not captured
-        ops = {**ops, "fp32": None}
+    if prec == "fp32r" and (v == 9 or (v == 6 and d == 4 and M <= 161)):
+        ops = OPS_PER_ENTRY_NOSLOT.get((prec, d))  # the slot-free form (order 4 of the 256 x 4 shape too)
     if ops:
         out.update(pipe_fracs(ops, n, ms, peaks, sms, sm_mhz))
     traffic = order5_traffic(prec, M) if d == 5 else None
