@@ -448,8 +448,9 @@ __device__ __forceinline__ void store_entry(const FwdArgs &a, int d, uint64_t id
 // YC > 0 (refined path only): no slot. Y(x) stays in shared memory for the
 // whole item and each Schur-complement block is formed where it is used
 // (su_block): the c3 pivots, z(x) and d(x) of the batch setup, and one block per
-// leaf pair and batch. That trades a few FP32 operations per leaf for the
-// slot's DRAM writes and re-reads.
+// leaf pair and batch. That trades FP32 work (about 60 more FP32 instructions
+// per order-5 leaf with a 384-entry x area) for the slot's DRAM writes and
+// re-reads.
 template <int D, int MODE, int PREC, int NT = TREE_THREADS, int XC = XCAP, bool DISP = false, bool CL = false,
           int CC = CCAP, int YC = 0>
 __device__ __forceinline__ void tree_item(const FwdArgs &a, TreeShared<D, XC, DISP, CC, YC> &sh, double *const slot,
